@@ -1,0 +1,157 @@
+"""Seeded synthetic inputs shared by the CPU oracle and the CUDA path.
+
+This module only draws numbers: cohesion fields with a weak inclusion and
+white noise, per-instance material draws for batches, and the named workload
+presets.  It holds none of the solver's arithmetic, so both sides can take
+their inputs from it without sharing any of the method.
+
+Random numbers come from one counter-based generator: the i-th output of
+splitmix64 started from ``seed`` (Steele, Lea and Flood, "Fast splittable
+pseudorandom number generators", OOPSLA 2014), mapped to a double in [0, 1)
+from its top 53 bits.  Draw i is a pure function of (seed, i), so every array
+is reproducible element by element.
+
+The workloads stand in for the paper's setups (a box under pure shear with a
+weak seed, Sec. 4.1): the paper used no dataset, so every input here is
+synthetic.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(seed: int, count: int, offset: int = 0) -> np.ndarray:
+    """Outputs offset..offset+count-1 of splitmix64 seeded with ``seed`` (uint64)."""
+    with np.errstate(over="ignore"):
+        idx = np.arange(offset + 1, offset + count + 1, dtype=np.uint64)
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + idx * _GAMMA
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform01(seed: int, count: int, offset: int = 0) -> np.ndarray:
+    """Doubles in [0, 1) from the top 53 bits of :func:`splitmix64`."""
+    z = splitmix64(seed, count, offset)
+    return (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+def cell_centres(n, L):
+    """Cell-centre coordinates per axis on the centred box [-L/2, L/2]."""
+    return [(-0.5 * L[d] + (np.arange(n[d]) + 0.5) * (L[d] / n[d])) for d in range(len(n))]
+
+
+def cohesion_field(n, L, c0, noise=0.01, seed=0, inclusion_radius=0.0,
+                   inclusion_centre=None, inclusion_factor=0.5):
+    """Per-cell cohesion c = c0 (1 + noise (2U - 1)), halved in a weak inclusion.
+
+    ``n`` and ``L`` have 2 or 3 entries.  The array is returned in C order with
+    x fastest, i.e. shape (ny, nx) or (nz, ny, nx); cell (i, j[, k]) draws
+    U number i + nx (j + ny k).  A cell belongs to the inclusion when its centre
+    lies within ``inclusion_radius`` of ``inclusion_centre`` (centre-sampled).
+    """
+    ndim = len(n)
+    count = int(np.prod(n))
+    u = uniform01(seed, count).reshape(tuple(reversed(n)))
+    c = c0 * (1.0 + noise * (2.0 * u - 1.0))
+    if inclusion_radius > 0.0:
+        centre = inclusion_centre if inclusion_centre is not None else [0.0] * ndim
+        axes = cell_centres(n, L)
+        grids = np.meshgrid(*reversed(axes), indexing="ij")  # (z,)y,x order
+        r2 = np.zeros_like(c)
+        for d in range(ndim):
+            r2 += (grids[ndim - 1 - d] - centre[d]) ** 2
+        c = np.where(r2 <= inclusion_radius ** 2, inclusion_factor * c, c)
+    return np.ascontiguousarray(c, dtype=np.float64)
+
+
+@dataclass
+class Setup:
+    """One solve: grid, material, loading and solver settings."""
+    name: str
+    ndim: int
+    n: tuple
+    L: tuple = (1.0, 1.0, 1.0)
+    K: float = 2.0
+    G: float = 1.0
+    mu_s: float = math.inf
+    phi_deg: float = 30.0
+    psi_deg: float = 0.0
+    c0: float = 1.5e-3
+    inclusion_radius: float = 0.05
+    inclusion_centre: tuple = (0.0, 0.0, 0.0)
+    noise: float = 0.01
+    seed: int = 0
+    a: float = 1.0
+    dt: float = 1e-4
+    load_plane: str = "xy"
+    increments: int = 30
+    tol: float = 1e-8
+    precision: str = "fp64"
+    extra: dict = field(default_factory=dict)
+
+    def cohesion(self) -> np.ndarray:
+        return cohesion_field(self.n, self.L[: self.ndim], self.c0, self.noise, self.seed,
+                              self.inclusion_radius, self.inclusion_centre[: self.ndim])
+
+
+def config(index: int, **overrides) -> Setup:
+    """The five named workloads (seeds: index * 1000 + instance).
+
+    1: 2D plane-strain elasto-plastic 64x64, 30 increments, tol 1e-8.
+    2: 2D visco-elasto-plastic 511x511, eta/(G dt) = 10, 200 increments.
+    3: 3D elasto-plastic 127^3 (oracle at 63^3), x-z pure shear, 100 increments.
+    4: batch of 256 uneven 2D instances (see :func:`batch_setups`).
+    5: 3D elasto-plastic 511^3, x-z pure shear, 60 increments, tol 1e-6.
+    """
+    if index == 1:
+        s = Setup("2d-64-ep", 2, (64, 64), seed=1000, increments=30, tol=1e-8)
+    elif index == 2:
+        s = Setup("2d-511-vep", 2, (511, 511), mu_s=1e-3, seed=2000, increments=200, tol=1e-8)
+    elif index == 3:
+        s = Setup("3d-127-ep", 3, (127, 127, 127), seed=3000, load_plane="xz",
+                  increments=100, tol=1e-6, precision="fp32")
+    elif index == 5:
+        s = Setup("3d-511-ep", 3, (511, 511, 511), seed=5000, load_plane="xz",
+                  increments=60, tol=1e-6, precision="fp32")
+    else:
+        raise ValueError("config %d has no single-grid setup; use batch_setups()" % index)
+    for k, v in overrides.items():
+        setattr(s, k, v)
+    return s
+
+
+BATCH_SIZES = (127, 255, 383, 511)
+
+
+def batch_setups(count: int = 256, base_seed: int = 4000, sizes=BATCH_SIZES) -> list:
+    """Instances of the uneven 2D batch: n, phi, c0 and the inclusion drawn per instance.
+
+    Instance b uses seed base_seed + b.  Its first five draws pick
+    n ~ U{sizes}, phi ~ U[20, 35] deg, c0 ~ U[1e-3, 2e-3] G, r ~ U[0.03, 0.08]
+    and the inclusion centre ~ U[-0.5 + r, 0.5 - r]^2 (two draws); the cohesion
+    noise uses the separate stream seeded with base_seed + b + 2^32.
+    """
+    out = []
+    for b in range(count):
+        seed = base_seed + b
+        u = uniform01(seed, 6)
+        n = sizes[min(int(u[0] * len(sizes)), len(sizes) - 1)]
+        phi = 20.0 + 15.0 * u[1]
+        c0 = 1e-3 + 1e-3 * u[2]
+        r = 0.03 + 0.05 * u[3]
+        cx = -0.5 + r + (1.0 - 2.0 * r) * u[4]
+        cy = -0.5 + r + (1.0 - 2.0 * r) * u[5]
+        s = Setup("batch-%d" % b, 2, (n, n), phi_deg=phi, c0=c0, inclusion_radius=r,
+                  inclusion_centre=(cx, cy, 0.0), seed=seed + (1 << 32), increments=50,
+                  tol=1e-6, precision="fp32")
+        out.append(s)
+    return out
