@@ -1,0 +1,351 @@
+#!/usr/bin/env python3
+"""Benchmark of the pseudo-transient elasto-plastic solve on GB300.
+
+Workload (default): the 3D elasto-plastic box of 511^3 cells under x-z pure
+shear with a spherical weak inclusion (radius 0.05, half cohesion) and +-1%
+seeded cohesion noise; K = 2, G = 1, c = 1.5e-3 G, phi = 30 deg, strain
+increment 1e-4, tolerance 1e-6.  One step is one load increment solved to
+tolerance (start state, pseudo-transient sweeps, FP64 commit): the first
+increment at which the inclusion yields, re-solved from a device checkpoint
+each step so that every step does the same work.
+
+Metric: effective HBM throughput of the sweeps (algorithmic bytes per cell
+per iteration x cells x iterations / wall time) and the wall time per
+increment.  With --gpus N (torchrun), each rank solves its own replica (the
+solve does not shard: no data-path collective) and value is the sum over
+ranks divided by the slowest rank's time.
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (a smaller grid of the same setup).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "HBM GB/s and wall time per increment to tol 1e-6: warm-start FP32 vs plain FP64"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--size", type=int, default=511, help="cells per side of the 3D box")
+    ap.add_argument("--increment", type=int, default=5, help="load increment that is timed")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--fp64-compare", action="store_true", help="also time the plain FP64 solve")
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-size", type=int, default=24)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def setup_for(size, tol):
+    import ep_inputs as E
+    return E.config(5, n=(size, size, size), tol=tol)
+
+
+# ---------------------------------------------------------------- clocks ----
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_%d.csv" % index)
+
+    def start(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax = float(p[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ oracle arm ----
+def oracle_increment_rate(size, tol, increment, max_seconds=30.0):
+    """Time the FP64 CPU oracle on the same setup at a small size.
+
+    Runs the elastic increments untimed, then times solving `increment`
+    (restoring the history first each repetition) until max_seconds is spent.
+    Returns (seconds per increment, iterations, cells)."""
+    import numpy as np
+    import oracle as O
+    s = setup_for(size, tol)
+    o = O.from_setup(s)
+    rates = [s.a, 0.0, -s.a]
+    for _ in range(increment - 1):
+        o.apply_increment(rates, s.dt)
+        o.solve_increment()
+    names = ("vx", "vy", "vz", "txx", "tyy", "tzz", "txy", "txz", "tyz", "p", "epl", "ux", "uy", "uz",
+             "exx", "eyy", "ezz", "exy", "exz", "eyz")
+    saved = {f: o.get(f) for f in names}
+    times, iters = [], 0
+    t_start = time.perf_counter()
+    while True:
+        for f, v in saved.items():
+            o.set(f, v)
+        t0 = time.perf_counter()
+        o.apply_increment(rates, s.dt)
+        info = o.solve_increment()
+        times.append(time.perf_counter() - t0)
+        iters = info["iters"]
+        if time.perf_counter() - t_start > max_seconds or len(times) >= 3:
+            break
+    del np
+    return sum(times) / len(times), iters, size ** 3
+
+
+def alg_bytes_per_cell(ndim, precision):
+    """Bytes one fused sweep iteration must move per cell."""
+    nd, ns = ndim, (3 if ndim == 3 else 1)
+    words = (nd + (nd + ns) + 1 + (nd + ns) + 1 + 1 + (ns + nd - 1)) + (nd + (nd + ns) + 1)
+    return words * (8 if precision == "fp64" else 4)
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    s = setup_for(args.size, args.tol)
+    # bounded sample: each step solves the timed increment on a cpu_size^3 grid
+    per_inc, iters, cells = None, None, None
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        per_inc, iters, cells = oracle_increment_rate(args.cpu_size, args.tol, args.increment, max_seconds=0.0)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    sec = sum(times) / len(times)
+    bpc = alg_bytes_per_cell(3, "fp64")
+    gbs = bpc * cells * iters / per_inc / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "3d-ep-xz-inclusion %d^3 (oracle sample of the %d^3 workload), increment %d, tol %g"
+                   % (args.cpu_size, s.n[0], args.increment, args.tol),
+                   "sample_cells": cells, "iterations": iters},
+        "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": "increment %d of the %d^3 box solved by the single-threaded FP64 oracle "
+                                   "(%d iterations, %.2f s per increment)" % (args.increment, args.cpu_size, iters,
+                                                                             per_inc)},
+        "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------- our arm ----
+def make_grid(P, s, precision):
+    g = P.Grid(3, s.n, s.L, precision=P.FP64 if precision == "fp64" else P.FP32_MIXED)
+    g.set_material(s.K, s.G, s.mu_s, s.phi_deg, s.psi_deg, s.cohesion())
+    g.set_solver(tol=s.tol, max_iter=2000000, n_chk=100)
+    return g
+
+
+def prepare(P, s, precision, increment):
+    g = make_grid(P, s, precision)
+    for _ in range(increment - 1):
+        g.apply_increment(s.a, s.dt, P.LOAD_XZ)
+        g.solve_increment()
+    g.snapshot()
+    return g
+
+
+def one_step(P, g, s):
+    g.restore()
+    g.apply_increment(s.a, s.dt, P.LOAD_XZ)
+    return g.solve_increment()
+
+
+def our_arm(args):
+    import torch
+    import paper_2305_01701_gb300 as P
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+
+    s = setup_for(args.size, args.tol)
+    cells = s.n[0] * s.n[1] * s.n[2]
+    g = prepare(P, s, args.precision, args.increment)
+    bpc = g.sweep_bytes_per_cell()
+    for _ in range(args.warmup):
+        info = one_step(P, g, s)
+    clk = Clocks(local)
+    barrier()
+    clk.start()
+    t0 = time.perf_counter()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    infos = []
+    for _ in range(args.steps):
+        infos.append(one_step(P, g, s))
+    ev1.record()
+    barrier()
+    wall = time.perf_counter() - t0
+    clocks = clk.stop()
+    # per-rank time: the host-side wall clock (the solve is synchronous per step)
+    tmax = wall
+    if dist:
+        t = torch.tensor([wall], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tmax = float(t.item())
+    iters = sum(i["iters"] for i in infos)
+    my_bytes = bpc * cells * iters
+    total_bytes = my_bytes * world
+    gbs = total_bytes / tmax / 1e9
+    ms_per_step = tmax / args.steps * 1e3
+
+    # kernel timing (CUDA events on the library's stream) for the roofline
+    ktimes = g.time_sweep(10)
+    kernels = ["strain", "trial", "return_centres", "return_edges", "velocity"]
+    it_ms = ktimes[-1]
+    dom = int(max(range(len(kernels)), key=lambda q: ktimes[q]))
+
+    # end-to-end through the C ABI with host buffers: scalars in, fields out
+    e2e = None
+    if args.e2e_steps > 0:
+        fields = ["vx", "vy", "vz", "epl"]
+        bufs = {f: torch.empty(g.count(f), dtype=torch.float64, pin_memory=True) for f in fields}
+        d2h = sum(b.numel() * 8 for b in bufs.values())
+        h2d = 8 * 3 + 8  # rates and dt
+        t0 = time.perf_counter()
+        e_iters = 0
+        for _ in range(args.e2e_steps):
+            g.restore()
+            g.apply_increment(s.a, s.dt, P.LOAD_XZ)
+            e_iters += g.solve_increment()["iters"]
+            for f in fields:
+                g.get_into(f, bufs[f].data_ptr(), bufs[f].numel())
+        et = time.perf_counter() - t0
+        e2e = {"value": bpc * cells * e_iters * world / et / 1e9, "unit": "GB/s",
+               "ms_per_step": et / args.e2e_steps * 1e3, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    fp64 = None
+    if args.fp64_compare:
+        g.close()
+        g64 = prepare(P, s, "fp64", args.increment)
+        t0 = time.perf_counter()
+        i64 = one_step(P, g64, s)
+        t64 = time.perf_counter() - t0
+        fp64 = {"ms_per_increment": t64 * 1e3, "iterations": i64["iters"],
+                "GB_per_s": g64.sweep_bytes_per_cell() * cells * i64["iters"] / t64 / 1e9}
+        g64.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        per_inc, c_iters, c_cells = oracle_increment_rate(args.cpu_size, args.tol, args.increment)
+        cpu = {"value": alg_bytes_per_cell(3, "fp64") * c_cells * c_iters / per_inc / 1e9, "unit": "GB/s",
+               "cores": 1, "kind": "oracle",
+               "sample": "increment %d of the same setup on a %d^3 grid, single-threaded FP64 oracle "
+                         "(%d iterations, %.2f s per increment)" % (args.increment, args.cpu_size, c_iters, per_inc)}
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    achieved = bpc * cells / (it_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": "whole sweep iteration (%d stage kernels, dominant: %s)"
+                                      % (len(kernels), kernels[dom]),
+            "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6800 GB/s",
+            "traffic": None, "kernel_ms": {k: float(ktimes[q]) for q, k in enumerate(kernels)},
+            "iteration_ms": float(it_ms), "alg_bytes_per_cell": bpc}
+    line = {
+        "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": "3d-ep-xz-inclusion %d^3, increment %d, tol %g, %s sweeps, plain start"
+                   % (s.n[0], args.increment, args.tol, args.precision),
+                   "cells": cells, "iterations_per_step": infos[-1]["iters"],
+                   "l2": "inputs larger than L2 (every field %.2f GB)" % (cells * 4 / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "ms_per_increment": ms_per_step,
+        "clocks": clocks,
+        # per step: (iters / n_chk + 1) graph chunks of 5 n_chk + 1 kernels, plus
+        # about 20 start-of-increment and 7 commit kernels
+        "gpu_launches": int(sum((i["iters"] // 100 + 1) * 501 + 27 for i in infos)),
+        "roofline": roof,
+        "e2e": e2e,
+        "fp64_plain": fp64,
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return our_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,186 @@
+/*
+ * ep.h -- C ABI of the GB300 pseudo-transient elasto-plastic solver.
+ *
+ * The library advances a (visco-)hypoelastic, perfectly plastic
+ * Drucker-Prager medium on a conservative staggered grid, one load increment
+ * at a time, with the accelerated pseudo-transient iteration of
+ * Alkhimenkov et al. (arXiv:2305.01701):
+ *   - governing equations: Eqs. A22S, A21S, A23S (Sec. 2.5);
+ *   - pseudo-transient form: Eqs. A22P, A2ssP, A23ssP (Sec. 3.2) with the
+ *     numerical parameters of Eqs. PT1-PT24qq;
+ *   - Jaumann rotation of the old stress: Eqs. j1-j14 and Appendix A;
+ *   - Drucker-Prager yield and return: Eqs. A6-A6121lambda, Sec. 3.3;
+ *   - pure-shear velocity walls with free slip: Eqs. A7-A9M (Sec. 4.1);
+ *   - L-infinity convergence measures: Eqs. Convergence1-3 (Sec. 4.2).
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns an ep_status; on failure ep_last_error() holds a
+ *     one-line reason.  A handle stays valid after EP_ERR_NOT_CONVERGED and
+ *     keeps its last iterate.
+ *   - Host arrays passed in are owned by the caller and copied before the
+ *     call returns.  Device memory is owned by the library, or lives in a
+ *     caller-provided workspace (see ep_create_grid).
+ *   - Field arrays are FP64, compact, x fastest, in the natural extent of
+ *     their staggered location: centres nx*ny[*nz]; x-faces (nx+1)*ny[*nz];
+ *     y-faces nx*(ny+1)[*nz]; z-faces nx*ny*(nz+1); 2D vertices and 3D
+ *     xy-edges (nx+1)*(ny+1)[*nz]; xz-edges (nx+1)*ny*(nz+1); yz-edges
+ *     nx*(ny+1)*(nz+1).  The box is [-Lx/2, Lx/2] x [-Ly/2, Ly/2] [x ...].
+ *   - Calls on one handle are not thread-safe; different handles are
+ *     independent.  All device work of a handle runs on its stream.
+ *   - No entry point launches work on a device other than the current one.
+ */
+#ifndef EP_H
+#define EP_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ep_grid *ep_handle;
+
+typedef enum {
+  EP_OK = 0,
+  EP_ERR_ARG = 1,            /* invalid argument (sizes, psi != 0, nulls)   */
+  EP_ERR_CUDA = 2,           /* a CUDA runtime call failed                  */
+  EP_ERR_OOM = 3,            /* device allocation failed / workspace short  */
+  EP_ERR_STATE = 4,          /* call out of order (e.g. solve w/o increment)*/
+  EP_ERR_NOT_CONVERGED = 5,  /* max_iter reached; state kept                */
+  EP_ERR_DIVERGED = 6,       /* NaN/Inf in a residual norm                  */
+  EP_ERR_TIMEOUT = 7         /* a bounded device wait gave up               */
+} ep_status;
+
+/* EP_FP64: every sweep in FP64.  EP_FP32_MIXED: sweeps in FP32 on the
+ * velocity increment of the current load increment, with FP64 residual
+ * norms, convergence test, start-of-increment base state and history. */
+typedef enum { EP_FP64 = 0, EP_FP32_MIXED = 1 } ep_precision;
+
+/* pure-shear loading planes (Eqs. A7-A9M): XY is v_x = a x, v_y = -a y
+ * (v_z = 0 in 3D); XZ is v_x = a x, v_z = -a z, v_y = 0 (3D only). */
+enum { EP_LOAD_XY = 0, EP_LOAD_XZ = 1 };
+
+/* field ids for ep_get_fields / ep_set_fields (FP64, layout above) */
+enum {
+  EP_VX = 0, EP_VY, EP_VZ,           /* converged velocity (faces)          */
+  EP_TXX, EP_TYY, EP_TZZ,            /* deviatoric stress, centres          */
+  EP_TXY, EP_TXZ, EP_TYZ,            /* deviatoric stress, vertices/edges   */
+  EP_P,                              /* pressure, centres                   */
+  EP_EPL,                            /* accumulated plastic strain, centres */
+  EP_UX, EP_UY, EP_UZ,               /* displacement (faces)                */
+  EP_EXX, EP_EYY, EP_EZZ,            /* accumulated total strain, centres   */
+  EP_EXY, EP_EXZ, EP_EYZ,            /* accumulated total strain, edges     */
+  EP_COH,                            /* cohesion, centres                   */
+  EP_EII,                            /* sqrt(eps:eps/2) of EXX..EYZ (read)  */
+  EP_SCALE,                          /* last return scale s, centres (read) */
+  EP_V0X, EP_V0Y, EP_V0Z,            /* start velocity of the increment     */
+  EP_FIELD_COUNT_ = 29
+};
+
+typedef struct {
+  double tol;           /* stop when eps_res <= tol                           */
+  long long max_iter;   /* iteration cap; a multiple of n_chk                 */
+  int n_chk;            /* residual check cadence (even, >= 2)                */
+  double c_cfl;         /* Vp = c_cfl * dx_min per pseudo step (0.9/sqrt(nd)) */
+  double xi;            /* multiplier of Re_opt = 3 sqrt(10) pi / 2 (1)       */
+  double r_pt;          /* K~/G~ of Eq. PT23 (r_opt = 1/2)                    */
+  int jaumann;          /* rotate the old stress (Eq. j1), default 1          */
+} ep_solver_opts;
+
+typedef struct {
+  long long iters;      /* iteration index of the converged check            */
+  double eps_res;       /* max(eps_mom, eps_tau, eps_p)                       */
+  double eps_mom;       /* dx_min max|R| / max|sigma|         (Eq. Conv.3)    */
+  double eps_tau;       /* max|d tau| / (1 - beta_tau) / max|sigma|           */
+  double eps_p;         /* max|d p| / (1 - beta_p) / max|sigma|               */
+  double eps_rel;       /* max|V - V_it| / max|V| between checks (Eq. Conv.2) */
+  double max_r;         /* max|R| over interior faces                         */
+  double max_sigma;     /* max|sigma_ij| over all components                  */
+  long long n_plastic;  /* centres with s < 1 at convergence                  */
+  double sxx_int_centre;/* integral of sigma_xx along the centre column       */
+  double sxx_int_right; /* the same along the rightmost column                */
+  double ms;            /* device wall time of the solve, milliseconds       */
+  int status;           /* ep_status of the solve                             */
+} ep_solve_info;
+
+/* Device bytes a grid needs.  Pass a buffer of at least this size to
+ * ep_create_grid to keep every device allocation in caller memory. */
+ep_status ep_workspace_bytes(int ndim, const int n[3], ep_precision prec, size_t *bytes);
+
+/* Create a grid of n[0] x n[1] (x n[2]) cells on a box of size L (Sec. 3.1).
+ * stream: a cudaStream_t or NULL (the library creates its own).
+ * workspace: NULL (the library allocates with cudaMalloc) or a device
+ * pointer of at least ep_workspace_bytes bytes, 256-byte aligned, owned by the
+ * caller and kept alive until ep_destroy.  ndim must be 2 or 3, n >= 1. */
+ep_status ep_create_grid(int ndim, const int n[3], const double L[3], ep_precision prec,
+                         void *stream, void *workspace, size_t workspace_bytes, ep_handle *out);
+
+/* Material (Sec. 2.2, Eqs. A43, A61, A611): bulk K and shear G moduli, shear
+ * viscosity mu_s (INFINITY = elastic limit), friction angle phi and dilation
+ * angle psi in degrees (psi must be 0, Eq. A6121lambda), and the per-cell
+ * cohesion (host, nx*ny[*nz] values, copied). */
+ep_status ep_set_material(ep_handle h, double K, double G, double mu_s, double phi_deg,
+                          double psi_deg, const double *cohesion);
+
+/* Fill opts with the defaults for a grid of dimension ndim. */
+ep_status ep_default_solver(int ndim, ep_solver_opts *opts);
+ep_status ep_set_solver(ep_handle h, const ep_solver_opts *opts);
+
+/* Start a load increment of length dt with pure shear at rate a in
+ * load_plane (Eqs. A7-A9M).  body_force: NULL or host face arrays
+ * concatenated x, y[, z] (Eq. A220).  use_warm_start: non-zero adds the
+ * attached warm-start predictor's velocity increment to the start. */
+ep_status ep_apply_increment(ep_handle h, double a, double dt, int load_plane,
+                             const double *body_force, int use_warm_start);
+
+/* The same with an arbitrary diagonal velocity gradient rates[0..2] and an
+ * optional host start increment dv_start (face arrays concatenated, walls
+ * ignored) added to the previous converged velocity. */
+ep_status ep_apply_increment_rates(ep_handle h, const double rates[3], double dt,
+                                   const double *body_force, const double *dv_start);
+
+/* Iterate the current increment to eps_res <= tol (or max_iter) and, on
+ * success, commit the history (the "old" fields of Fig. 1).  info may be
+ * NULL.  Returns EP_ERR_NOT_CONVERGED / EP_ERR_DIVERGED without committing. */
+ep_status ep_solve_increment(ep_handle h, ep_solve_info *info);
+
+/* Commit the current iterate as the increment's result (used after a
+ * deliberate fixed-iteration solve). */
+ep_status ep_commit_increment(ep_handle h);
+
+/* Copy one FP64 field to/from host memory; count must equal the field's
+ * size (ep_field_count).  ep_set_fields accepts history fields only. */
+ep_status ep_field_count(ep_handle h, int field, size_t *count);
+ep_status ep_get_fields(ep_handle h, int field, double *host_out, size_t count);
+ep_status ep_set_fields(ep_handle h, int field, const double *host_in, size_t count);
+
+/* Device-resident checkpoint of the FP64 history (velocity, deviator,
+ * pressure, plastic strain, displacement, accumulated strain).  The first
+ * ep_snapshot allocates the checkpoint with cudaMalloc (freed by ep_destroy);
+ * ep_restore copies it back, so the next increment starts from the saved
+ * state.  Both run on the grid's stream and return after it has drained. */
+ep_status ep_snapshot(ep_handle h);
+ep_status ep_restore(ep_handle h);
+
+/* Profiling: run `iters` pseudo-time sweeps (no residual checks) from the
+ * current state on the grid's stream, timing each kernel with CUDA events.
+ * ms_out[0..n_out-1] receives the mean milliseconds per launch of each sweep
+ * kernel in launch order, followed by the mean milliseconds of one whole
+ * iteration; n_kernels (nullable) receives the number of sweep kernels.
+ * The sweep state afterwards is unspecified: call it between increments. */
+ep_status ep_time_sweep(ep_handle h, int iters, double *ms_out, int n_out, int *n_kernels);
+
+/* Algorithmic bytes one sweep iteration must move per cell in the grid's
+ * precision (the fused-sweep lower bound: every state array read and
+ * written once, every constant read once). */
+ep_status ep_sweep_bytes_per_cell(ep_handle h, double *bytes);
+
+ep_status ep_destroy(ep_handle h);
+
+/* Last error message of h, or of the calling thread when h is NULL. */
+const char *ep_last_error(ep_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EP_H */

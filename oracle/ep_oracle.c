@@ -38,7 +38,9 @@
  *  - each iteration starts from the stress consistent with the start
  *    velocity (one pseudo step with no relaxation memory);
  *  - the stopping test takes the largest of the three equations' residuals,
- *    each in stress units and relative to max|sigma|, every n_chk iterations.
+ *    each in stress units and relative to max|sigma|, every n_chk iterations;
+ *    the deviator and pressure residuals are their pseudo-time rates averaged
+ *    over the check interval.
  */
 #include <math.h>
 #include <stdint.h>
@@ -94,6 +96,7 @@ typedef struct {
   /* pseudo-time state: velocity, deviator, pressure */
   double *v0[3], *vi[3], *vchk[3];
   double *tn_k[3], *ts_k[3], *p_k;
+  double *tn_c[3], *ts_c[3], *p_c;   /* stress state at the previous check */
   /* quantities of the last evaluation */
   double *en[3], *es[3], *om[3], *div;
   double *tJn[3], *tJs[3];
@@ -149,7 +152,7 @@ or_grid *or_create(int ndim, const int *n, const double *L) {
   g->c_cfl = 0.9 / sqrt((double)ndim); g->xi = 1.0; g->r_pt = 0.5; g->jaumann = 1;
   long nc = n_centres(g);
   g->coh = zalloc(nc); g->p = zalloc(nc); g->epl = zalloc(nc); g->div = zalloc(nc);
-  g->pc = zalloc(nc); g->s = zalloc(nc); g->p_k = zalloc(nc);
+  g->pc = zalloc(nc); g->s = zalloc(nc); g->p_k = zalloc(nc); g->p_c = zalloc(nc);
   for (int d = 0; d < 3; ++d) {
     long nf = d < ndim ? n_face(g, d) : 0;
     g->v[d] = zalloc(nf); g->u[d] = zalloc(nf); g->v0[d] = zalloc(nf); g->vi[d] = zalloc(nf);
@@ -157,17 +160,18 @@ or_grid *or_create(int ndim, const int *n, const double *L) {
     long nn = d < ndim ? nc : 0;
     g->tn[d] = zalloc(nn); g->an[d] = zalloc(nn); g->en[d] = zalloc(nn); g->tn_k[d] = zalloc(nn);
     g->tJn[d] = zalloc(nn); g->trn[d] = zalloc(nn); g->Tn[d] = zalloc(nn); g->sn[d] = zalloc(nn);
+    g->tn_c[d] = zalloc(nn);
     long ns = (ndim == 3 || d == 0) ? n_shear(g, d) : 0;
     g->ts[d] = zalloc(ns); g->as[d] = zalloc(ns); g->es[d] = zalloc(ns); g->om[d] = zalloc(ns);
     g->ts_k[d] = zalloc(ns); g->tJs[d] = zalloc(ns); g->trs[d] = zalloc(ns); g->Ts[d] = zalloc(ns);
-    g->ss[d] = zalloc(ns);
+    g->ss[d] = zalloc(ns); g->ts_c[d] = zalloc(ns);
   }
   return g;
 }
 
 void or_destroy(or_grid *g) {
   if (!g) return;
-  free(g->coh); free(g->p); free(g->epl); free(g->div); free(g->pc); free(g->s); free(g->p_k);
+  free(g->coh); free(g->p); free(g->epl); free(g->div); free(g->pc); free(g->s); free(g->p_k); free(g->p_c);
   for (int d = 0; d < 3; ++d) {
     free(g->v[d]); free(g->u[d]); free(g->v0[d]); free(g->vi[d]); free(g->vchk[d]);
     free(g->R[d]); free(g->f[d]);
@@ -175,6 +179,7 @@ void or_destroy(or_grid *g) {
     free(g->trn[d]); free(g->Tn[d]); free(g->sn[d]);
     free(g->ts[d]); free(g->as[d]); free(g->es[d]); free(g->om[d]); free(g->ts_k[d]);
     free(g->tJs[d]); free(g->trs[d]); free(g->Ts[d]); free(g->ss[d]);
+    free(g->tn_c[d]); free(g->ts_c[d]);
   }
   free(g);
 }
@@ -573,8 +578,11 @@ int or_set_start(or_grid *g, const double *v) {
   return OR_OK;
 }
 
-/* L-infinity norms (Eq. Convergence1) of the last evaluation. */
-static void norms(const or_grid *g, double *max_r, double *max_sig, double *d_tau, double *d_p) {
+/* L-infinity norms (Eq. Convergence1) of the last evaluation: max|R|,
+ * max|sigma|, and the largest change of the deviator and of the pressure
+ * since the previous check (the stress state saved then).  When `refresh`
+ * is set the saved state becomes the new one. */
+static void norms(or_grid *g, double *max_r, double *max_sig, double *d_tau, double *d_p, int refresh) {
   double mr = 0.0, ms = 0.0, dtau = 0.0, dp = 0.0;
   int nan_seen = 0;
   for (int d = 0; d < g->ndim; ++d) {
@@ -588,19 +596,30 @@ static void norms(const or_grid *g, double *max_r, double *max_sig, double *d_ta
   for (long c = 0; c < nc; ++c) {
     for (int d = 0; d < g->ndim; ++d) {
       double a = fabs(g->sn[d][c] - g->pc[c]); if (a > ms) ms = a;
-      double b = fabs(g->sn[d][c] - g->tn_k[d][c]); if (b > dtau) dtau = b;
+      double b = fabs(g->sn[d][c] - g->tn_c[d][c]); if (b > dtau) dtau = b;
+      if (refresh) g->tn_c[d][c] = g->sn[d][c];
     }
-    double b = fabs(g->pc[c] - g->p_k[c]); if (b > dp) dp = b;
+    double b = fabs(g->pc[c] - g->p_c[c]); if (b > dp) dp = b;
+    if (refresh) g->p_c[c] = g->pc[c];
   }
   for (int s = 0; s < n_shear_comp(g); ++s) {
     long ns = n_shear(g, s);
     for (long e = 0; e < ns; ++e) {
       double a = fabs(g->ss[s][e]); if (a > ms) ms = a;
-      double b = fabs(g->ss[s][e] - g->ts_k[s][e]); if (b > dtau) dtau = b;
+      double b = fabs(g->ss[s][e] - g->ts_c[s][e]); if (b > dtau) dtau = b;
+      if (refresh) g->ts_c[s][e] = g->ss[s][e];
     }
   }
   if (nan_seen) mr = NAN;
   *max_r = mr; *max_sig = ms; *d_tau = dtau; *d_p = dp;
+}
+
+/* copy the pseudo-time stress state into the check snapshot */
+static void snapshot_state(or_grid *g) {
+  long nc = n_centres(g);
+  memcpy(g->p_c, g->p_k, sizeof(double) * nc);
+  for (int d = 0; d < g->ndim; ++d) memcpy(g->tn_c[d], g->tn_k[d], sizeof(double) * nc);
+  for (int s = 0; s < n_shear_comp(g); ++s) memcpy(g->ts_c[s], g->ts_k[s], sizeof(double) * n_shear(g, s));
 }
 
 static void diagnostics(or_grid *g, or_info *info) {
@@ -631,11 +650,15 @@ static void diagnostics(or_grid *g, or_info *info) {
  *   1. p_{k+1}, tau_{k+1} from one pseudo step of Eqs. A2ssP/A23ssP and the
  *      return, using v_k;
  *   2. R_k = div(tau_{k+1} - p_{k+1} I) + f (Eq. A22S);
- *   3. at k = 0 and every n_chk-th k: eps_mom = dx_min max|R| / max|sigma|,
- *      eps_tau = max|tau_{k+1} - tau_k| / (1 - beta_tau) / max|sigma|,
- *      eps_p = max|p_{k+1} - p_k| / (1 - beta_p) / max|sigma| (each equation's
- *      residual in stress units), eps_res = max of the three; stop when
- *      eps_res <= tol, keeping (v_k, tau_{k+1}, p_{k+1});
+ *   3. at k = 0 and every n_chk-th k, with m the iterations since the previous
+ *      check (m = 1 at k = 0, whose reference state is the start state):
+ *      eps_mom = dx_min max|R| / max|sigma|,
+ *      eps_tau = max|tau_{k+1} - tau_chk| / (m (1 - beta_tau)) / max|sigma|,
+ *      eps_p = max|p_{k+1} - p_chk| / (m (1 - beta_p)) / max|sigma|
+ *      (each equation's residual in stress units, the pseudo-time rates taken
+ *      over the check interval as eps_rel takes V - V^it, Eq. Convergence2),
+ *      eps_res = the largest; stop when eps_res <= tol, keeping
+ *      (v_k, tau_{k+1}, p_{k+1});
  *   4. v_{k+1} = v_k + R_k / rho~ at interior faces (Eq. A22P). */
 int or_solve_increment(or_grid *g, or_info *info) {
   if (!g->in_increment) return OR_ERR_STATE;
@@ -649,16 +672,20 @@ int or_solve_increment(or_grid *g, or_info *info) {
   /* start stress: physical response to v0 */
   evaluate(g, g->vi, 0.0, 0.0);
   accept_stress(g);
+  snapshot_state(g);
   const double dxm = dx_min(g);
   int status = OR_ERR_NOT_CONVERGED;
+  long k_prev = -1;
   for (long k = 0;; ++k) {
     evaluate(g, g->vi, q.beta_tau, q.beta_p);
     if (k % g->n_chk == 0 || k == g->max_iter) {
       double mr, ms, dtau, dp;
-      norms(g, &mr, &ms, &dtau, &dp);
+      norms(g, &mr, &ms, &dtau, &dp, 1);
+      const double m = (double)(k - k_prev);
+      k_prev = k;
       double em = (mr == 0.0) ? 0.0 : (ms > 0.0 ? dxm * mr / ms : INFINITY);
-      double et = (dtau == 0.0) ? 0.0 : (ms > 0.0 ? dtau / (1.0 - q.beta_tau) / ms : INFINITY);
-      double ep = (dp == 0.0) ? 0.0 : (ms > 0.0 ? dp / (1.0 - q.beta_p) / ms : INFINITY);
+      double et = (dtau == 0.0) ? 0.0 : (ms > 0.0 ? dtau / (m * (1.0 - q.beta_tau)) / ms : INFINITY);
+      double ep = (dp == 0.0) ? 0.0 : (ms > 0.0 ? dp / (m * (1.0 - q.beta_p)) / ms : INFINITY);
       double er = em > et ? em : et;
       if (ep > er) er = ep;
       double dvm = 0.0, vm = 0.0;
@@ -703,7 +730,7 @@ int or_eval(or_grid *g, const double *v, double *max_r, double *max_sig) {
   evaluate(g, g->vi, 0.0, 0.0);
   accept_stress(g);
   double dtau, dp;
-  norms(g, max_r, max_sig, &dtau, &dp);
+  norms(g, max_r, max_sig, &dtau, &dp, 0);
   return OR_OK;
 }
 

@@ -1,0 +1,12 @@
+"""GB300-native pseudo-transient solver for strain localization in a
+(visco-)hypoelastic, perfectly plastic Drucker-Prager medium
+(Alkhimenkov, Khakimova, Utkin, Podladchikov, arXiv:2305.01701).
+
+The compute path is the CUDA library ``lib/libep.so`` (C ABI in
+``include/ep.h``); this package only marshals arguments to it.
+"""
+from ._native import (FP32_MIXED, FP64, LOAD_XY, LOAD_XZ, EPError, Grid, field_shape, lib,
+                      workspace_bytes)
+
+__all__ = ["Grid", "EPError", "FP64", "FP32_MIXED", "LOAD_XY", "LOAD_XZ", "field_shape", "lib",
+           "workspace_bytes"]

@@ -1,0 +1,243 @@
+"""ctypes binding of ``lib/libep.so`` (the C ABI declared in ``include/ep.h``).
+
+Argument marshalling only: every step of the solve runs in the library's
+CUDA kernels.  Importing this module fails loudly when the library has not
+been built; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libep.so")
+
+OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_STATE, ERR_NOT_CONVERGED, ERR_DIVERGED, ERR_TIMEOUT = range(8)
+STATUS_NAMES = {0: "EP_OK", 1: "EP_ERR_ARG", 2: "EP_ERR_CUDA", 3: "EP_ERR_OOM", 4: "EP_ERR_STATE",
+                5: "EP_ERR_NOT_CONVERGED", 6: "EP_ERR_DIVERGED", 7: "EP_ERR_TIMEOUT"}
+FP64, FP32_MIXED = 0, 1
+LOAD_XY, LOAD_XZ = 0, 1
+
+FIELDS = ["vx", "vy", "vz", "txx", "tyy", "tzz", "txy", "txz", "tyz", "p", "epl",
+          "ux", "uy", "uz", "exx", "eyy", "ezz", "exy", "exz", "eyz", "coh", "eii", "scale",
+          "v0x", "v0y", "v0z"]
+FIELD_ID = {n: i for i, n in enumerate(FIELDS)}
+
+
+class SolverOpts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_iter", C.c_longlong), ("n_chk", C.c_int),
+                ("c_cfl", C.c_double), ("xi", C.c_double), ("r_pt", C.c_double), ("jaumann", C.c_int)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iters", C.c_longlong), ("eps_res", C.c_double), ("eps_mom", C.c_double),
+                ("eps_tau", C.c_double), ("eps_p", C.c_double), ("eps_rel", C.c_double),
+                ("max_r", C.c_double), ("max_sigma", C.c_double), ("n_plastic", C.c_longlong),
+                ("sxx_int_centre", C.c_double), ("sxx_int_right", C.c_double), ("ms", C.c_double),
+                ("status", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class EPError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+_lib = None
+
+# (name, restype, argtypes) of every exported entry point of include/ep.h
+_P, _D, _I, _Z = C.c_void_p, C.c_double, C.c_int, C.c_size_t
+_DP = C.POINTER(C.c_double)
+_IP = C.POINTER(C.c_int)
+SIGNATURES = [
+    ("ep_workspace_bytes", _I, [_I, _IP, _I, C.POINTER(C.c_size_t)]),
+    ("ep_create_grid", _I, [_I, _IP, _DP, _I, _P, _P, _Z, C.POINTER(_P)]),
+    ("ep_set_material", _I, [_P, _D, _D, _D, _D, _D, _DP]),
+    ("ep_default_solver", _I, [_I, C.POINTER(SolverOpts)]),
+    ("ep_set_solver", _I, [_P, C.POINTER(SolverOpts)]),
+    ("ep_apply_increment", _I, [_P, _D, _D, _I, _DP, _I]),
+    ("ep_apply_increment_rates", _I, [_P, _DP, _D, _DP, _DP]),
+    ("ep_solve_increment", _I, [_P, C.POINTER(SolveInfo)]),
+    ("ep_commit_increment", _I, [_P]),
+    ("ep_field_count", _I, [_P, _I, C.POINTER(C.c_size_t)]),
+    ("ep_get_fields", _I, [_P, _I, _DP, _Z]),
+    ("ep_set_fields", _I, [_P, _I, _DP, _Z]),
+    ("ep_snapshot", _I, [_P]),
+    ("ep_restore", _I, [_P]),
+    ("ep_time_sweep", _I, [_P, _I, _DP, _I, _IP]),
+    ("ep_sweep_bytes_per_cell", _I, [_P, _DP]),
+    ("ep_destroy", _I, [_P]),
+    ("ep_last_error", C.c_char_p, [_P]),
+]
+
+
+def lib():
+    """Load libep.so (raises if it is missing: build it with ``build.build()``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libep.so not built at %s; run __graft_entry__.build() or "
+                              "paper_2305_01701_gb300.build.build()" % LIB_PATH)
+        L = C.CDLL(LIB_PATH)
+        for name, res, args in SIGNATURES:
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _dp(a):
+    return None if a is None else a.ctypes.data_as(_DP)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64).ravel()
+
+
+def check(h, st):
+    if st != OK:
+        msg = lib().ep_last_error(h)
+        raise EPError(st, msg.decode() if msg else "")
+    return st
+
+
+def field_shape(ndim, n, name):
+    """Natural C-order shape of a field (x fastest), matching include/ep.h."""
+    nx, ny = n[0], n[1]
+    nz = n[2] if ndim == 3 else 1
+    faces = {"x": (nx + 1, ny, nz), "y": (nx, ny + 1, nz), "z": (nx, ny, nz + 1)}
+    if name in ("vx", "ux", "v0x", "vy", "uy", "v0y", "vz", "uz", "v0z"):
+        ex, ey, ez = faces[name[-1]]
+    elif name in ("txy", "exy"):
+        ex, ey, ez = nx + 1, ny + 1, nz
+    elif name in ("txz", "exz"):
+        ex, ey, ez = nx + 1, ny, nz + 1
+    elif name in ("tyz", "eyz"):
+        ex, ey, ez = nx, ny + 1, nz + 1
+    else:
+        ex, ey, ez = nx, ny, nz
+    return (ez, ey, ex) if ndim == 3 else (ey, ex)
+
+
+def workspace_bytes(ndim, n, precision=FP64):
+    nn = (C.c_int * 3)(*(list(n[:ndim]) + [1] * (3 - ndim)))
+    out = C.c_size_t()
+    check(None, lib().ep_workspace_bytes(ndim, nn, precision, C.byref(out)))
+    return out.value
+
+
+class Grid:
+    """One staggered grid solved on the GPU through the C ABI.
+
+    ``stream``: an integer cudaStream_t handle (e.g.
+    ``torch.cuda.current_stream().cuda_stream``) or None.  ``workspace``: an
+    integer device pointer of at least :func:`workspace_bytes` bytes (e.g. the
+    data_ptr of a torch uint8 tensor the caller keeps alive) or None.
+    """
+
+    def __init__(self, ndim, n, L=(1.0, 1.0, 1.0), precision=FP64, stream=None, workspace=None,
+                 workspace_size=0):
+        self._L = lib()
+        self.ndim = ndim
+        self.n = tuple(int(x) for x in n[:ndim])
+        self.precision = precision
+        nn = (C.c_int * 3)(*(list(self.n) + [1] * (3 - ndim)))
+        ll = _f64(list(L[:ndim]) + [1.0] * (3 - ndim))
+        h = _P()
+        st = self._L.ep_create_grid(ndim, nn, _dp(ll), precision, stream, workspace, workspace_size, C.byref(h))
+        check(None, st)
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._L.ep_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def set_material(self, K, G, mu_s, phi_deg, psi_deg, cohesion):
+        c = _f64(cohesion)
+        check(self.h, self._L.ep_set_material(self.h, K, G, mu_s, phi_deg, psi_deg, _dp(c)))
+
+    def default_solver(self):
+        o = SolverOpts()
+        check(self.h, self._L.ep_default_solver(self.ndim, C.byref(o)))
+        return o
+
+    def set_solver(self, tol=1e-8, max_iter=10000000, n_chk=100, c_cfl=None, xi=1.0, r_pt=0.5, jaumann=True):
+        o = self.default_solver()
+        o.tol = tol
+        o.max_iter = int(max_iter)
+        o.n_chk = int(n_chk)
+        o.c_cfl = c_cfl if c_cfl is not None else 0.9 / math.sqrt(self.ndim)
+        o.xi = xi
+        o.r_pt = r_pt
+        o.jaumann = int(bool(jaumann))
+        check(self.h, self._L.ep_set_solver(self.h, C.byref(o)))
+
+    def apply_increment(self, a, dt, load_plane=LOAD_XY, body_force=None, use_warm_start=False):
+        f = None if body_force is None else _f64(np.concatenate([_f64(b) for b in body_force]))
+        check(self.h, self._L.ep_apply_increment(self.h, a, dt, load_plane, _dp(f), int(use_warm_start)))
+
+    def apply_increment_rates(self, rates, dt, body_force=None, dv_start=None):
+        r = _f64(list(rates) + [0.0] * (3 - len(rates)))
+        f = None if body_force is None else _f64(np.concatenate([_f64(b) for b in body_force]))
+        dv = None if dv_start is None else _f64(np.concatenate([_f64(b) for b in dv_start]))
+        check(self.h, self._L.ep_apply_increment_rates(self.h, _dp(r), dt, _dp(f), _dp(dv)))
+
+    def solve_increment(self, raise_on_fail=True):
+        info = SolveInfo()
+        st = self._L.ep_solve_increment(self.h, C.byref(info))
+        if raise_on_fail:
+            check(self.h, st)
+        d = info.as_dict()
+        d["status"] = st
+        return d
+
+    def commit_increment(self):
+        check(self.h, self._L.ep_commit_increment(self.h))
+
+    def count(self, name):
+        c = C.c_size_t()
+        check(self.h, self._L.ep_field_count(self.h, FIELD_ID[name], C.byref(c)))
+        return c.value
+
+    def get(self, name):
+        n = self.count(name)
+        out = np.empty(n, dtype=np.float64)
+        check(self.h, self._L.ep_get_fields(self.h, FIELD_ID[name], _dp(out), n))
+        return out.reshape(field_shape(self.ndim, self.n + (1,), name))
+
+    def snapshot(self):
+        check(self.h, self._L.ep_snapshot(self.h))
+
+    def restore(self):
+        check(self.h, self._L.ep_restore(self.h))
+
+    def get_into(self, name, host_ptr, count):
+        """Copy a field into caller memory at host_ptr (e.g. pinned torch storage)."""
+        check(self.h, self._L.ep_get_fields(self.h, FIELD_ID[name], C.cast(host_ptr, _DP), count))
+
+    def time_sweep(self, iters=10):
+        """Mean ms per launch of each sweep kernel, then of a whole iteration."""
+        out = np.zeros(16, dtype=np.float64)
+        nk = C.c_int()
+        check(self.h, self._L.ep_time_sweep(self.h, int(iters), _dp(out), 16, C.byref(nk)))
+        return out[: nk.value + 1].copy()
+
+    def sweep_bytes_per_cell(self):
+        b = C.c_double()
+        check(self.h, self._L.ep_sweep_bytes_per_cell(self.h, C.byref(b)))
+        return b.value
+
+    def set(self, name, arr):
+        a = _f64(arr)
+        check(self.h, self._L.ep_set_fields(self.h, FIELD_ID[name], _dp(a), a.size))

@@ -1,0 +1,273 @@
+"""GPU path (through the C ABI) against the FP64 CPU oracle.
+
+FP64: every field within 1e-10 of the oracle, L-infinity normalised
+(max|gpu - oracle| / max|oracle|, since pointwise ratios are undefined at
+zeros), and the same iteration counts.  FP32 mixed: the stated bounds of
+1e-5 on stress and 1e-4 on plastic strain (L-infinity normalised).
+Sizes span several thread blocks and ragged edges (odd, non-square grids).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import ep_inputs as E
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+FIELDS_2D = ("vx", "vy", "txx", "tyy", "txy", "p", "epl", "ux", "uy", "exx", "eyy", "exy")
+FIELDS_3D = ("vx", "vy", "vz", "txx", "tyy", "tzz", "txy", "txz", "tyz", "p", "epl", "ux", "uy", "uz",
+             "exx", "eyy", "ezz", "exy", "exz", "eyz")
+
+
+@pytest.fixture(scope="module")
+def P():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2305_01701_gb300 import build as B
+    B.build()
+    import paper_2305_01701_gb300 as P
+    return P
+
+
+def rel_err(a, b, scale=0.0):
+    """max|a - b| / max(max|b|, scale)."""
+    den = max(np.abs(b).max(), scale)
+    return np.abs(a - b).max() / den if den > 0 else np.abs(a - b).max()
+
+
+GROUPS = {"stress": ("txx", "tyy", "tzz", "txy", "txz", "tyz", "p"), "velocity": ("vx", "vy", "vz"),
+          "displacement": ("ux", "uy", "uz"), "strain": ("exx", "eyy", "ezz", "exy", "exz", "eyz"),
+          "plastic": ("epl",)}
+
+
+def group_scales(o, fields):
+    """L-infinity scale of each field's physical group, from the oracle: a
+    field is normalised by the largest component of its group (a pressure
+    that is zero up to rounding is judged against the stress magnitude)."""
+    sc = {}
+    for names in GROUPS.values():
+        present = [f for f in names if f in fields]
+        m = max([np.abs(o.get(f)).max() for f in present] + [0.0])
+        for f in present:
+            sc[f] = m
+    return sc
+
+
+def rates_of(s):
+    return [s.a, -s.a] if s.ndim == 2 else ([s.a, -s.a, 0.0] if s.load_plane == "xy" else [s.a, 0.0, -s.a])
+
+
+def gpu_grid(P, s, precision, **solver):
+    g = P.Grid(s.ndim, s.n, s.L, precision=precision)
+    g.set_material(s.K, s.G, s.mu_s, s.phi_deg, s.psi_deg, s.cohesion())
+    kw = dict(tol=s.tol)
+    kw.update(solver)
+    g.set_solver(**kw)
+    return g
+
+
+def run_pair(P, s, increments, precision=None, fields=None, tol_fields=1e-10, same_iters=True, **solver):
+    precision = P.FP64 if precision is None else precision
+    g = gpu_grid(P, s, precision, **solver)
+    o = O.from_setup(s, **solver)
+    fields = fields or (FIELDS_2D if s.ndim == 2 else FIELDS_3D)
+    worst = {}
+    for inc in range(1, increments + 1):
+        g.apply_increment_rates(rates_of(s), s.dt)
+        ig = g.solve_increment()
+        o.apply_increment(rates_of(s), s.dt)
+        io = o.solve_increment()
+        if same_iters:
+            assert ig["iters"] == io["iters"], (inc, ig, io)
+        assert ig["n_plastic"] == io["n_plastic"] or not same_iters, (inc, ig["n_plastic"], io["n_plastic"])
+        sc = group_scales(o, fields)
+        for f in fields:
+            e = rel_err(g.get(f), o.get(f), sc[f])
+            worst[f] = max(worst.get(f, 0.0), e)
+            if tol_fields is not None:
+                assert e <= tol_fields, (inc, f, e)
+    g.close()
+    return worst
+
+
+def test_homogeneous_elastic_closed_form_2d(P):
+    s = E.config(1, n=(37, 29), noise=0.0, inclusion_radius=0.0, c0=1.0)
+    g = gpu_grid(P, s, P.FP64)
+    for inc in range(1, 4):
+        g.apply_increment(1.0, 1e-4, P.LOAD_XY)
+        info = g.solve_increment()
+        assert info["iters"] == 0
+        np.testing.assert_allclose(g.get("txx"), 2e-4 * inc, rtol=1e-13)
+        np.testing.assert_allclose(g.get("tyy"), -2e-4 * inc, rtol=1e-13)
+        assert np.abs(g.get("txy")).max() < 1e-18
+
+
+def test_fp64_parity_2d_inclusion_through_first_yield(P):
+    """2D weak inclusion with noise, 40x33 cells (ragged), through the first
+    plastic increments: iteration counts equal, every field <= 1e-10."""
+    s = E.config(1, n=(40, 33))
+    run_pair(P, s, 8)
+
+
+def test_fp64_parity_2d_64_config1_first_increments(P):
+    s = E.config(1)
+    run_pair(P, s, 7)
+
+
+def test_fp64_parity_2d_maxwell(P):
+    """Visco-elasto-plastic (mu_s / (G dt) = 10) on a ragged 48x35 grid."""
+    s = E.config(2, n=(48, 35), increments=14)
+    run_pair(P, s, 14)
+
+
+def test_fp64_parity_fixed_iterations_2d(P):
+    """A deliberately unconverged fixed-iteration solve (tol 0, 300 iterations)
+    on the first plastic increment compares the raw iteration with the
+    oracle's, state included."""
+    s = E.config(1, n=(33, 31), tol=1e-10)
+    g = gpu_grid(P, s, P.FP64)
+    o = O.from_setup(s)
+    for inc in range(1, 6):
+        if inc == 5:
+            g.set_solver(tol=0.0, max_iter=300, n_chk=100)
+            o.set_solver(tol=0.0, max_iter=300, n_chk=100)
+        g.apply_increment(1.0, s.dt, P.LOAD_XY)
+        o.apply_increment([1.0, -1.0], s.dt)
+        ig = g.solve_increment(raise_on_fail=False)
+        io = o.solve_increment(commit=False, raise_on_fail=False)
+        if ig["status"] != 0:
+            g.commit_increment()
+        if io["status"] != 0:
+            o.commit()
+        else:
+            o.commit()
+        assert ig["iters"] == io["iters"], inc
+    assert ig["status"] == 5 and io["status"] == 5
+    sc = group_scales(o, FIELDS_2D)
+    for f in FIELDS_2D:
+        assert rel_err(g.get(f), o.get(f), sc[f]) <= 1e-11, f
+
+
+def test_fp64_parity_3d_ragged(P):
+    """3D x-z pure shear with a spherical inclusion on a ragged 17x13x11 grid."""
+    s = E.config(3, n=(17, 13, 11), tol=1e-9, precision="fp64", inclusion_radius=0.15)
+    run_pair(P, s, 8)
+
+
+def test_fp64_parity_3d_xy_loading_jaumann_off(P):
+    s = E.config(3, n=(12, 14, 10), tol=1e-9, precision="fp64", load_plane="xy", inclusion_radius=0.2)
+    run_pair(P, s, 7, jaumann=False)
+
+
+def test_fp64_parity_tiny_and_degenerate_grids(P):
+    """1x1 (no interior faces), 2x2, 3x1 and 1x1x1 / 2x2x2."""
+    for nd, n in ((2, (1, 1)), (2, (2, 2)), (2, (3, 1)), (3, (1, 1, 1)), (3, (2, 2, 2))):
+        s = E.Setup("tiny", nd, n, inclusion_radius=0.0, noise=0.01, seed=5, tol=1e-11,
+                    load_plane="xz" if nd == 3 else "xy")
+        run_pair(P, s, 9)
+
+
+def test_fp64_body_force_manufactured(P):
+    sp = pytest.importorskip("sympy")
+    from test_oracle_pins import _mms_2d
+    (vxe, vye), (bx, by), dt = _mms_2d(24)
+    s = E.Setup("mms", 2, (24, 24), c0=1.0, inclusion_radius=0.0, noise=0.0, tol=1e-11, dt=dt)
+    g = gpu_grid(P, s, P.FP64)
+    o = O.from_setup(s)
+    g.apply_increment_rates([1.0, -1.0], dt, body_force=(bx, by))
+    o.apply_increment([1.0, -1.0], dt, body_force=(bx, by))
+    ig, io = g.solve_increment(), o.solve_increment()
+    assert ig["iters"] == io["iters"]
+    fl = ("vx", "vy", "txx", "tyy", "txy", "p")
+    sc = group_scales(o, fl)
+    for f in fl:
+        assert rel_err(g.get(f), o.get(f), sc[f]) <= 1e-10, f
+    del sp
+
+
+def test_fp32_mixed_within_stated_bounds_2d(P):
+    s = E.config(1, n=(48, 40), tol=1e-8)
+    worst = run_pair(P, s, 8, precision=P.FP32_MIXED, tol_fields=None, same_iters=False, max_iter=200000)
+    for f in ("txx", "tyy", "txy", "p"):
+        assert worst[f] <= 1e-5, (f, worst[f])
+    assert worst["epl"] <= 1e-4, worst["epl"]
+
+
+def test_fp32_mixed_within_stated_bounds_3d(P):
+    s = E.config(3, n=(16, 15, 14), tol=1e-8, inclusion_radius=0.15)
+    worst = run_pair(P, s, 7, precision=P.FP32_MIXED, tol_fields=None, same_iters=False, max_iter=200000)
+    for f in ("txx", "tyy", "tzz", "txy", "txz", "tyz", "p"):
+        assert worst[f] <= 1e-5, (f, worst[f])
+    assert worst["epl"] <= 1e-4, worst["epl"]
+
+
+def test_not_converged_keeps_state_and_reports(P):
+    s = E.config(1, n=(32, 32))
+    g = gpu_grid(P, s, P.FP64, max_iter=200, n_chk=100, tol=1e-14)
+    for _ in range(6):
+        g.apply_increment(1.0, s.dt, P.LOAD_XY)
+        info = g.solve_increment(raise_on_fail=False)
+    assert info["status"] == 5 and info["iters"] == 200
+    with pytest.raises(P.EPError):
+        g.solve_increment()  # still open: hits max_iter again
+    g.commit_increment()
+
+
+def test_argument_and_state_errors(P):
+    with pytest.raises(P.EPError):
+        P.Grid(2, (0, 5))
+    g = P.Grid(2, (8, 8))
+    with pytest.raises(P.EPError):
+        g.apply_increment(1.0, 1e-4)            # no material yet
+    with pytest.raises(P.EPError):
+        g.set_material(2.0, 1.0, math.inf, 30.0, 5.0, np.ones(64))   # psi != 0
+    g.set_material(2.0, 1.0, math.inf, 30.0, 0.0, np.ones(64))
+    with pytest.raises(P.EPError):
+        g.solve_increment()                     # no open increment
+    with pytest.raises(P.EPError):
+        g.set_solver(n_chk=3)                   # odd cadence
+    with pytest.raises(P.EPError):
+        g.apply_increment(1.0, 1e-4, P.LOAD_XZ)  # x-z loading needs 3D
+
+
+def test_resume_from_fields_is_bit_identical(P):
+    s = E.config(1, n=(24, 24))
+    a = gpu_grid(P, s, P.FP64)
+    for _ in range(5):
+        a.apply_increment(1.0, s.dt, P.LOAD_XY); a.solve_increment()
+    hist = ("vx", "vy", "txx", "tyy", "txy", "p", "epl", "ux", "uy", "exx", "eyy", "exy")
+    saved = {f: a.get(f) for f in hist}
+    b = gpu_grid(P, s, P.FP64)
+    for f, v in saved.items():
+        b.set(f, v)
+    for _ in range(2):
+        a.apply_increment(1.0, s.dt, P.LOAD_XY); ia = a.solve_increment()
+        b.apply_increment(1.0, s.dt, P.LOAD_XY); ib = b.solve_increment()
+        assert ia["iters"] == ib["iters"]
+    for f in hist:
+        assert np.array_equal(a.get(f), b.get(f)), f
+
+
+def test_torch_workspace_and_stream(P):
+    """Device memory and the stream come from PyTorch; the solve runs in the
+    library's kernels on that stream."""
+    import torch
+    s = E.config(1, n=(20, 18))
+    nbytes = P.workspace_bytes(2, s.n, P.FP64)
+    ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+    ptr = (ws.data_ptr() + 255) // 256 * 256
+    st = torch.cuda.Stream()
+    g = P.Grid(2, s.n, precision=P.FP64, stream=st.cuda_stream, workspace=ptr, workspace_size=nbytes)
+    g.set_material(s.K, s.G, s.mu_s, s.phi_deg, s.psi_deg, s.cohesion())
+    g.set_solver(tol=s.tol)
+    o = O.from_setup(s)
+    for _ in range(6):
+        g.apply_increment(1.0, s.dt, P.LOAD_XY); g.solve_increment()
+        o.apply_increment([1.0, -1.0], s.dt); o.solve_increment()
+    assert rel_err(g.get("txx"), o.get("txx")) <= 1e-10
+    assert rel_err(g.get("p"), o.get("p"), np.abs(o.get("txx")).max()) <= 1e-10
+    g.close()
+    del ws
