@@ -154,6 +154,81 @@ ep_status ep_field_count(ep_handle h, int field, size_t *count);
 ep_status ep_get_fields(ep_handle h, int field, double *host_out, size_t count);
 ep_status ep_set_fields(ep_handle h, int field, const double *host_in, size_t count);
 
+/* Sweep kernel selection.  EP_KERNEL_AUTO (default): the fused one-kernel
+ * sweep for FP32 grids, the staged five-kernel sweep for FP64 ones (FP64 is
+ * bound by FP64 arithmetic on GB300, where the staged sweep does no halo
+ * recomputation).  EP_KERNEL_STAGED / EP_KERNEL_FUSED force one; a body force
+ * always uses the staged sweep.  shape (< 0 keeps the current): in 3D the
+ * z-planes per block of the fused kernel (>= 1); in 2D the tile of the fused
+ * kernel (0: 32x8, 1: 32x16, 2: 64x8 cells). */
+enum { EP_KERNEL_AUTO = -1, EP_KERNEL_STAGED = 0, EP_KERNEL_FUSED = 1 };
+ep_status ep_set_kernel(ep_handle h, int variant, int shape);
+
+/* Batched 2D solves: many grids of any sizes and materials advance through
+ * one persistent kernel per iteration (each block strides over (grid, tile)
+ * work items; grids that have converged drop out), captured with the
+ * per-grid residual checks into one CUDA graph per chunk of n_chk
+ * iterations.  The grids must be 2D, share a precision and n_chk, and stay
+ * alive until ep_destroy_batch; the batch runs on the first grid's stream.
+ * A grid solved in a batch performs the same arithmetic as when solved
+ * alone with the fused 2D kernel. */
+typedef struct ep_batch *ep_batch_handle;
+ep_status ep_create_batch(const ep_handle *grids, int count, ep_batch_handle *out);
+/* start an increment in every grid: pure shear at rate a[i] (host array of
+ * count rates) over dt, in the x-y plane */
+ep_status ep_batch_apply_increment(ep_batch_handle b, const double *a, double dt);
+/* iterate every grid to its tolerance and commit those that converged;
+ * infos (nullable) receives count records; returns EP_ERR_NOT_CONVERGED /
+ * EP_ERR_DIVERGED if any grid did not converge (the others are committed) */
+ep_status ep_batch_solve_increment(ep_batch_handle b, ep_solve_info *infos);
+/* time `iters` sweeps of each tile shape on the open increments, keep the
+ * fastest (written to *tile_out when non-null) and restart the increments */
+ep_status ep_batch_autotune(ep_batch_handle b, int iters, int *tile_out);
+ep_status ep_batch_set_tile(ep_batch_handle b, int tile);
+ep_status ep_destroy_batch(ep_batch_handle b);
+
+/* Learned warm start.  A convolutional U-Net (hand-written CUDA forward,
+ * backward and Adam kernels; BF16 weights, FP32 accumulation and master
+ * weights) predicts an increment's velocity change from the previous ones.
+ * Layers: `levels` encoder levels of two 3^D convolutions + ReLU with
+ * base * 2^l channels and average pooling, a mirrored decoder with nearest
+ * upsampling and skip concatenation, and a zero-initialised 1^D head.
+ * Tensors are FP32 device arrays N x C x [Z x] Y x X (x fastest); spatial
+ * sizes must be multiples of 2^(levels-1). */
+typedef struct ep_net *ep_net_handle;
+ep_status ep_net_create(int ndim, int in_ch, int out_ch, int base, int levels, unsigned long long seed,
+                        void *stream, ep_net_handle *out);
+ep_status ep_net_param_count(ep_net_handle n, long long *count);
+ep_status ep_net_get_params(ep_net_handle n, float *host, long long count);
+ep_status ep_net_set_params(ep_net_handle n, const float *host, long long count);
+/* y (device, N x out_ch x ...) = net(x); size = {X, Y[, Z]} */
+ep_status ep_net_forward(ep_net_handle n, const float *x, int N, const int size[3], float *y);
+/* MSE loss mean((net(x) - t)^2) and its parameter gradient (host, nullable) */
+ep_status ep_net_gradients(ep_net_handle n, const float *x, const float *t, int N, const int size[3],
+                           double *loss, float *grad_host, long long count);
+/* one Adam step (beta 0.9 / 0.999) on the MSE loss; loss (nullable, host) */
+ep_status ep_net_train_step(ep_net_handle n, const float *x, const float *t, int N, const int size[3], float lr,
+                            double *loss);
+ep_status ep_net_destroy(ep_net_handle n);
+const char *ep_net_last_error(ep_net_handle n);
+
+/* Attach a network (ndim spatial dims, ndim + 2 inputs, ndim outputs; NULL
+ * detaches) used by ep_apply_increment(..., use_warm_start = 1).  Features
+ * at cell centres, on a grid padded to multiples of 4: the previous
+ * increment's velocity change (centre average per component) over its
+ * L-infinity norm S, then 1 - s (the last return scale), then c / max(c).
+ * The start velocity becomes v + S (dv_prev + net output interpolated to the
+ * faces); with fewer than two committed increments the plain start is used.
+ * The network does not change the converged answer, only the start. */
+ep_status ep_attach_warm_start(ep_handle h, ep_net_handle net);
+/* The features of the next increment (device, (ndim + 2) x padded size) and
+ * their scale S; dims receives the padded size {X, Y, Z}. */
+ep_status ep_warm_features(ep_handle h, float *dev_out, double *scale, int dims[3]);
+/* After a solve: the training target for features f taken before it
+ * (device, ndim x padded size): centre average of the committed velocity
+ * change over S, minus the feature channels of the previous change. */
+ep_status ep_warm_target(ep_handle h, const float *features, double scale, float *dev_out);
+
 /* Device-resident checkpoint of the FP64 history (velocity, deviator,
  * pressure, plastic strain, displacement, accumulated strain).  The first
  * ep_snapshot allocates the checkpoint with cudaMalloc (freed by ep_destroy);

@@ -39,8 +39,8 @@
  *    velocity (one pseudo step with no relaxation memory);
  *  - the stopping test takes the largest of the three equations' residuals,
  *    each in stress units and relative to max|sigma|, every n_chk iterations;
- *    the deviator and pressure residuals are their pseudo-time rates averaged
- *    over the check interval.
+ *    each residual is the pseudo-time rate of its state (velocity, deviator,
+ *    pressure) averaged over the check interval.
  */
 #include <math.h>
 #include <stdint.h>
@@ -652,7 +652,8 @@ static void diagnostics(or_grid *g, or_info *info) {
  *   2. R_k = div(tau_{k+1} - p_{k+1} I) + f (Eq. A22S);
  *   3. at k = 0 and every n_chk-th k, with m the iterations since the previous
  *      check (m = 1 at k = 0, whose reference state is the start state):
- *      eps_mom = dx_min max|R| / max|sigma|,
+ *      eps_mom = dx_min max|v_{k+1} - v_chk| rho~ / m / max|sigma| (the
+ *      momentum residual averaged over the interval; v_{k+1} = v_k + R_k/rho~),
  *      eps_tau = max|tau_{k+1} - tau_chk| / (m (1 - beta_tau)) / max|sigma|,
  *      eps_p = max|p_{k+1} - p_chk| / (m (1 - beta_p)) / max|sigma|
  *      (each equation's residual in stress units, the pseudo-time rates taken
@@ -683,20 +684,26 @@ int or_solve_increment(or_grid *g, or_info *info) {
       norms(g, &mr, &ms, &dtau, &dp, 1);
       const double m = (double)(k - k_prev);
       k_prev = k;
-      double em = (mr == 0.0) ? 0.0 : (ms > 0.0 ? dxm * mr / ms : INFINITY);
+      /* velocity after this iteration's update, compared with the one after
+       * the previous check's update: the momentum residual averaged over the
+       * check interval is rho~ (v_{k+1} - v_chk) / m (Eq. A22P) */
+      double dvm = 0.0, vm = 0.0;
+      for (int d = 0; d < g->ndim; ++d) {
+        int ex, ey, ez; face_dims(g, d, &ex, &ey, &ez);
+        for (int kk = 0; kk < ez; ++kk) for (int j = 0; j < ey; ++j) for (int i = 0; i < ex; ++i) {
+          long id = ((long)kk * ey + j) * ex + i;
+          double vn = g->vi[d][id];
+          if (!is_boundary_face(g, d, i, j, kk)) vn = g->vi[d][id] + q.vstep * g->R[d][id];
+          double a = fabs(vn - g->vchk[d][id]); if (a > dvm || a != a) dvm = a;
+          double b = fabs(g->vi[d][id]); if (b > vm) vm = b;
+          g->vchk[d][id] = vn;
+        }
+      }
+      double em = (dvm == 0.0) ? 0.0 : (ms > 0.0 ? dxm * dvm / (m * q.vstep) / ms : INFINITY);
       double et = (dtau == 0.0) ? 0.0 : (ms > 0.0 ? dtau / (m * (1.0 - q.beta_tau)) / ms : INFINITY);
       double ep = (dp == 0.0) ? 0.0 : (ms > 0.0 ? dp / (m * (1.0 - q.beta_p)) / ms : INFINITY);
       double er = em > et ? em : et;
       if (ep > er) er = ep;
-      double dvm = 0.0, vm = 0.0;
-      for (int d = 0; d < g->ndim; ++d) {
-        long nf = n_face(g, d);
-        for (long i = 0; i < nf; ++i) {
-          double a = fabs(g->vi[d][i] - g->vchk[d][i]); if (a > dvm) dvm = a;
-          double b = fabs(g->vi[d][i]); if (b > vm) vm = b;
-          g->vchk[d][i] = g->vi[d][i];
-        }
-      }
       info->iters = k; info->eps_res = er; info->eps_mom = em; info->eps_tau = et; info->eps_p = ep;
       info->max_r = mr; info->max_sigma = ms;
       info->eps_rel = vm > 0.0 ? dvm / vm : 0.0;

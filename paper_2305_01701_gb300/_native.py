@@ -20,6 +20,7 @@ STATUS_NAMES = {0: "EP_OK", 1: "EP_ERR_ARG", 2: "EP_ERR_CUDA", 3: "EP_ERR_OOM", 
                 5: "EP_ERR_NOT_CONVERGED", 6: "EP_ERR_DIVERGED", 7: "EP_ERR_TIMEOUT"}
 FP64, FP32_MIXED = 0, 1
 LOAD_XY, LOAD_XZ = 0, 1
+KERNEL_AUTO, KERNEL_STAGED, KERNEL_FUSED = -1, 0, 1
 
 FIELDS = ["vx", "vy", "vz", "txx", "tyy", "tzz", "txy", "txz", "tyz", "p", "epl",
           "ux", "uy", "uz", "exx", "eyy", "ezz", "exy", "exz", "eyz", "coh", "eii", "scale",
@@ -68,6 +69,25 @@ SIGNATURES = [
     ("ep_field_count", _I, [_P, _I, C.POINTER(C.c_size_t)]),
     ("ep_get_fields", _I, [_P, _I, _DP, _Z]),
     ("ep_set_fields", _I, [_P, _I, _DP, _Z]),
+    ("ep_set_kernel", _I, [_P, _I, _I]),
+    ("ep_create_batch", _I, [C.POINTER(_P), _I, C.POINTER(_P)]),
+    ("ep_batch_apply_increment", _I, [_P, _DP, _D]),
+    ("ep_batch_solve_increment", _I, [_P, C.POINTER(SolveInfo)]),
+    ("ep_batch_autotune", _I, [_P, _I, _IP]),
+    ("ep_batch_set_tile", _I, [_P, _I]),
+    ("ep_destroy_batch", _I, [_P]),
+    ("ep_net_create", _I, [_I, _I, _I, _I, _I, C.c_ulonglong, _P, C.POINTER(_P)]),
+    ("ep_net_param_count", _I, [_P, C.POINTER(C.c_longlong)]),
+    ("ep_net_get_params", _I, [_P, C.POINTER(C.c_float), C.c_longlong]),
+    ("ep_net_set_params", _I, [_P, C.POINTER(C.c_float), C.c_longlong]),
+    ("ep_net_forward", _I, [_P, _P, _I, _IP, _P]),
+    ("ep_net_gradients", _I, [_P, _P, _P, _I, _IP, C.POINTER(C.c_double), C.POINTER(C.c_float), C.c_longlong]),
+    ("ep_net_train_step", _I, [_P, _P, _P, _I, _IP, C.c_float, C.POINTER(C.c_double)]),
+    ("ep_net_destroy", _I, [_P]),
+    ("ep_net_last_error", C.c_char_p, [_P]),
+    ("ep_attach_warm_start", _I, [_P, _P]),
+    ("ep_warm_features", _I, [_P, _P, C.POINTER(C.c_double), _IP]),
+    ("ep_warm_target", _I, [_P, _P, _D, _P]),
     ("ep_snapshot", _I, [_P]),
     ("ep_restore", _I, [_P]),
     ("ep_time_sweep", _I, [_P, _I, _DP, _I, _IP]),
@@ -216,8 +236,29 @@ class Grid:
         check(self.h, self._L.ep_get_fields(self.h, FIELD_ID[name], _dp(out), n))
         return out.reshape(field_shape(self.ndim, self.n + (1,), name))
 
+    def set_kernel(self, variant=-1, kz=0):
+        """-1 auto, 0 staged (five kernels), 1 fused (one kernel, 3D); kz planes per block."""
+        check(self.h, self._L.ep_set_kernel(self.h, int(variant), int(kz)))
+
     def snapshot(self):
         check(self.h, self._L.ep_snapshot(self.h))
+
+    def attach_warm_start(self, net):
+        check(self.h, self._L.ep_attach_warm_start(self.h, net.h if net is not None else None))
+
+    def warm_dims(self):
+        p = [(x + 3) // 4 * 4 for x in self.n]
+        return tuple(p + [1] * (3 - len(p)))
+
+    def warm_features(self, out_ptr):
+        """Write the next increment's features to device memory at out_ptr; returns S."""
+        sc = C.c_double()
+        dims = (C.c_int * 3)()
+        check(self.h, self._L.ep_warm_features(self.h, out_ptr, C.byref(sc), dims))
+        return sc.value
+
+    def warm_target(self, feat_ptr, scale, out_ptr):
+        check(self.h, self._L.ep_warm_target(self.h, feat_ptr, scale, out_ptr))
 
     def restore(self):
         check(self.h, self._L.ep_restore(self.h))
@@ -241,3 +282,107 @@ class Grid:
     def set(self, name, arr):
         a = _f64(arr)
         check(self.h, self._L.ep_set_fields(self.h, FIELD_ID[name], _dp(a), a.size))
+
+
+class Batch:
+    """Many 2D grids advanced by one persistent kernel per iteration.
+
+    The grids stay owned by the caller (keep them alive while the batch is
+    used); they must be 2D and share precision and n_chk.
+    """
+
+    def __init__(self, grids):
+        self._L = lib()
+        self.grids = list(grids)
+        arr = (_P * len(self.grids))(*[g.h for g in self.grids])
+        b = _P()
+        check(None, self._L.ep_create_batch(arr, len(self.grids), C.byref(b)))
+        self.h = b
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._L.ep_destroy_batch(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def apply_increment(self, a, dt):
+        rates = _f64(a if np.ndim(a) else [a] * len(self.grids))
+        check(None, self._L.ep_batch_apply_increment(self.h, _dp(rates), dt))
+
+    def solve_increment(self, raise_on_fail=True):
+        infos = (SolveInfo * len(self.grids))()
+        st = self._L.ep_batch_solve_increment(self.h, infos)
+        if raise_on_fail:
+            check(None, st)
+        return [i.as_dict() for i in infos], st
+
+    def autotune(self, iters=20):
+        t = C.c_int()
+        check(None, self._L.ep_batch_autotune(self.h, int(iters), C.byref(t)))
+        return t.value
+
+    def set_tile(self, tile):
+        check(None, self._L.ep_batch_set_tile(self.h, int(tile)))
+
+
+def _ncheck(n, st):
+    if st != OK:
+        msg = lib().ep_net_last_error(n)
+        raise EPError(st, msg.decode() if msg else "")
+
+
+class Net:
+    """The warm-start U-Net (device parameters; tensors are device pointers)."""
+
+    def __init__(self, ndim, in_ch, out_ch, base=32, levels=3, seed=0, stream=None):
+        self._L = lib()
+        self.ndim, self.in_ch, self.out_ch, self.base, self.levels = ndim, in_ch, out_ch, base, levels
+        h = _P()
+        _ncheck(None, self._L.ep_net_create(ndim, in_ch, out_ch, base, levels, seed, stream, C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._L.ep_net_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def n_params(self):
+        c = C.c_longlong()
+        _ncheck(self.h, self._L.ep_net_param_count(self.h, C.byref(c)))
+        return c.value
+
+    def get_params(self):
+        n = self.n_params()
+        out = np.empty(n, dtype=np.float32)
+        _ncheck(self.h, self._L.ep_net_get_params(self.h, out.ctypes.data_as(C.POINTER(C.c_float)), n))
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _ncheck(self.h, self._L.ep_net_set_params(self.h, p.ctypes.data_as(C.POINTER(C.c_float)), p.size))
+
+    @staticmethod
+    def _size(size):
+        return (C.c_int * 3)(*(list(size) + [1] * (3 - len(size))))
+
+    def forward(self, x_ptr, N, size, y_ptr):
+        _ncheck(self.h, self._L.ep_net_forward(self.h, x_ptr, N, self._size(size), y_ptr))
+
+    def gradients(self, x_ptr, t_ptr, N, size):
+        n = self.n_params()
+        g = np.empty(n, dtype=np.float32)
+        loss = C.c_double()
+        _ncheck(self.h, self._L.ep_net_gradients(self.h, x_ptr, t_ptr, N, self._size(size), C.byref(loss),
+                                                  g.ctypes.data_as(C.POINTER(C.c_float)), n))
+        return loss.value, g
+
+    def train_step(self, x_ptr, t_ptr, N, size, lr):
+        loss = C.c_double()
+        _ncheck(self.h, self._L.ep_net_train_step(self.h, x_ptr, t_ptr, N, self._size(size), float(lr),
+                                                   C.byref(loss)))
+        return loss.value

@@ -55,6 +55,20 @@ struct ep_grid {
   double *dline = nullptr;
   cudaGraphExec_t chunk = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  int variant = EP_KERNEL_AUTO;  // sweep kernel choice (ep_set_kernel)
+  int kz = 64;              // z-planes per CTA of the fused 3D kernel
+  int tile = 0;             // tile of the fused 2D kernel (0: 32x8, 1: 32x16, 2: 64x8)
+  void *inst_dev = nullptr; // this grid as a batch of one (fused 2D)
+  int4 *items_dev = nullptr;
+  int n_items = 0, items_tile = -1, max_items = 0;
+  double last_rate[3] = {0, 0, 0};
+  // learned warm start
+  double *vpp[3] = {};          // converged velocity of the increment before last
+  int n_commits = 0;
+  double cmax = 1.0;
+  ep_net *net = nullptr;
+  float *wx = nullptr, *wy = nullptr;   // network input / output (cudaMalloc on attach)
+  unsigned long long *wscale = nullptr;
   char *snap = nullptr;     // checkpoint of the history (ep_snapshot)
   bool snap_started = false;
   std::string err;
@@ -123,6 +137,7 @@ void carve(ep_grid *h, Arena &a) {
     if (es == 8) p = a.take<double>(B); else p = a.take<float>(B);
   };
   for (int d = 0; d < nd; ++d) {
+    h->vpp[d] = a.take<double>(B);
     h->H.v[d] = a.take<double>(B); h->H.u[d] = a.take<double>(B); h->H.v0[d] = a.take<double>(B);
     h->H.tn[d] = a.take<double>(B); h->H.an[d] = a.take<double>(B);
     h->Tn64[d] = a.take<double>(B); h->stn64[d] = a.take<double>(B);
@@ -150,8 +165,12 @@ void carve(ep_grid *h, Arena &a) {
   if (nd == 3) tk(h->rd[1]);
   h->dscal = a.take<Scal>(1);
   h->dinfo = a.take<DevInfo>(1);
+  h->inst_dev = a.take<Inst2<double>>(1);
+  h->max_items = ((h->g.px + 31) / 32) * ((h->g.py + 7) / 8);
+  h->items_dev = a.take<int4>(h->max_items);
   h->dnpl = a.take<unsigned long long>(1);
   h->dline = a.take<double>(2);
+  h->wscale = a.take<unsigned long long>(1);
 }
 
 // natural extent of a field id; returns false for an unknown / absent field
@@ -272,6 +291,65 @@ Stage<T> sweep_stage(ep_grid *h, int b) {
   return S;
 }
 
+// This grid as one instance of the batched fused 2D kernel.
+template <typename T>
+Inst2<T> make_inst(ep_grid *h, DevInfo *di) {
+  Inst2<T> I{};
+  I.g = h->g;
+  I.sc = h->dscal;
+  I.di = di;
+  for (int b = 0; b < 2; ++b) {
+    for (int d = 0; d < 2; ++d) { I.u[b][d] = P<T>(h->u[b][d]); I.sn[b][d] = P<T>(h->stn[b][d]); }
+    I.ss[b] = P<T>(h->sts[b][0]);
+    I.sp[b] = P<T>(h->stp[b]);
+  }
+  for (int d = 0; d < 2; ++d) {
+    I.tbn[d] = P<T>(h->tbn[d]); I.uchk[d] = P<T>(h->uchk[d]); I.cn[d] = P<T>(h->cn[d]); I.v0[d] = h->H.v0[d];
+  }
+  I.tbs = P<T>(h->tbs[0]); I.pb = P<T>(h->pb); I.yc = P<T>(h->yc); I.rq = P<T>(h->rq[0]); I.rd = P<T>(h->rd[0]);
+  I.s = P<T>(h->s); I.cs = P<T>(h->cs[0]); I.cp = P<T>(h->cp);
+  return I;
+}
+
+// (instance, tile_x, tile_y) work items covering the padded box of a grid
+void append_items(std::vector<int4> &v, int inst, const Geo &g, int tile) {
+  int tx, ty;
+  fused2d_tile(tile, &tx, &ty);
+  for (int j = 0; j < (g.py + ty - 1) / ty; ++j)
+    for (int i = 0; i < (g.px + tx - 1) / tx; ++i) v.push_back(make_int4(inst, i, j, 0));
+}
+
+template <typename T>
+bool use_fused2d(const ep_grid *h) {
+  if (h->ndim != 2 || h->have_f) return false;
+  return h->variant == EP_KERNEL_FUSED || (h->variant == EP_KERNEL_AUTO && sizeof(T) == 4);
+}
+
+// upload this grid's instance record and work items for its tile
+template <typename T>
+ep_status prepare_solo2d(ep_grid *h) {
+  Inst2<T> I = make_inst<T>(h, h->dinfo);
+  CK(h, cudaMemcpyAsync(h->inst_dev, &I, sizeof(I), cudaMemcpyHostToDevice, h->stream));
+  if (h->items_tile != h->tile) {
+    std::vector<int4> it;
+    append_items(it, 0, h->g, h->tile);
+    if ((int)it.size() > h->max_items) return fail(h, EP_ERR_ARG, "work-item list larger than reserved");
+    CK(h, cudaMemcpyAsync(h->items_dev, it.data(), it.size() * sizeof(int4), cudaMemcpyHostToDevice, h->stream));
+    h->n_items = (int)it.size();
+    h->items_tile = h->tile;
+  }
+  CK(h, cudaStreamSynchronize(h->stream));
+  return EP_OK;
+}
+
+int persistent_blocks(int tile, size_t elem) {
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int per = elem == 4 ? fused2d_blocks_per_sm<float>(tile) : fused2d_blocks_per_sm<double>(tile);
+  return sms * per;
+}
+
 // FP64 physical response at face field v (beta = 0, base = c2 tau_hat).
 Stage<double> phys_stage(ep_grid *h, double *const v[3]) {
   Stage<double> S{};
@@ -343,16 +421,39 @@ ep_status prologue(ep_grid *h, const double *const dv[3]) {
   return EP_OK;
 }
 
+// The fused kernel serves FP32 3D sweeps without a body force.
+template <typename T>
+bool use_fused(const ep_grid *h) {
+  if (h->ndim != 3 || h->have_f) return false;
+  return h->variant == EP_KERNEL_FUSED || (h->variant == EP_KERNEL_AUTO && sizeof(T) == 4);
+}
+
 // One chunk of n_chk iterations (first one a check iteration), captured once.
 template <typename T>
 ep_status capture_chunk(ep_grid *h) {
   if (h->chunk) return EP_OK;
   const Geo &g = h->g;
   cudaGraph_t graph;
+  const bool f2 = use_fused2d<T>(h);
+  int blocks = 0;
+  if (f2) {
+    ep_status r = prepare_solo2d<T>(h);
+    if (r != EP_OK) return r;
+    blocks = std::min(persistent_blocks(h->tile, sizeof(T)), h->n_items);
+  }
   CK(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
-  for (int it = 0; it < h->opts.n_chk; ++it) {
+  for (int it = 0; f2 && it < h->opts.n_chk; ++it) {
+    launch_fused2d<T>(h->tile, (const Inst2<T> *)h->inst_dev, h->items_dev, h->n_items, it & 1, it == 0, blocks,
+                      h->cap);
+    if (it == 0) launch_check_batch<T>((const Inst2<T> *)h->inst_dev, 1, h->cap);
+  }
+  for (int it = 0; !f2 && it < h->opts.n_chk; ++it) {
     Stage<T> S = sweep_stage<T>(h, it & 1);
     const int chk = it == 0;
+    if (!chk && use_fused<T>(h)) {
+      launch_fused3d<T>(g, S, h->dscal, h->dinfo, h->kz, h->cap);
+      continue;
+    }
     launch_strain<T>(g, S, h->dscal, h->dinfo, h->cap);
     launch_trial<T>(g, S, h->dscal, h->dinfo, h->cap);
     launch_return_centres<T>(g, S, h->dscal, h->dinfo, chk, h->cap);
@@ -374,6 +475,8 @@ ep_status commit(ep_grid *h) {
   const Geo &g = h->g;
   cudaStream_t st = h->stream;
   const T *uf[3] = {P<T>(h->u[0][0]), P<T>(h->u[0][1]), P<T>(h->u[0][2])};
+  for (int d = 0; d < h->ndim; ++d)
+    CK(h, cudaMemcpyAsync(h->vpp[d], h->H.v[d], g.box * sizeof(double), cudaMemcpyDeviceToDevice, st));
   launch_compose<T>(g, h->H.v0, uf, h->H.v, st);
   Stage<double> S = phys_stage(h, h->H.v);
   launch_strain<double>(g, S, h->dscal, nullptr, st);
@@ -386,6 +489,7 @@ ep_status commit(ep_grid *h) {
   launch_line_integrals(g, h->H, h->dline, st);
   CK(h, cudaGetLastError());
   h->in_increment = false;
+  h->n_commits += 1;
   return EP_OK;
 }
 
@@ -525,6 +629,10 @@ ep_status ep_create_grid(int ndim, const int n[3], const double L[3], ep_precisi
     ep_destroy(h);
     return fail(nullptr, EP_ERR_CUDA, "ep_create_grid: stream/event/pinned allocation failed");
   }
+  if (fused3d_configure() != cudaSuccess || fused2d_configure() != cudaSuccess) {
+    ep_destroy(h);
+    return fail(nullptr, EP_ERR_CUDA, "ep_create_grid: fused kernel shared-memory attribute");
+  }
   e = cudaMemsetAsync(h->arena, 0, h->arena_bytes, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
@@ -551,6 +659,9 @@ ep_status ep_set_material(ep_handle h, double K, double G, double mu_s, double p
   }
   ep_status r = upload_box(h, cohesion, h->H.coh, h->g.nx, h->g.ny, h->g.nz);
   if (r != EP_OK) return r;
+  double cm = 0.0;
+  for (long long q = 0; q < (long long)h->g.nx * h->g.ny * h->g.nz; ++q) cm = std::max(cm, fabs(cohesion[q]));
+  h->cmax = cm > 0.0 ? cm : 1.0;
   h->have_material = true;
   return EP_OK;
 }
@@ -569,8 +680,8 @@ ep_status ep_set_solver(ep_handle h, const ep_solver_opts *o) {
   return EP_OK;
 }
 
-static ep_status apply_common(ep_handle h, const double rates[3], double dt, const double *body_force,
-                              const double *dv_start) {
+// validation, per-increment scalars and the body force of a new increment
+static ep_status set_increment(ep_grid *h, const double rates[3], double dt, const double *body_force) {
   if (!h) return fail(nullptr, EP_ERR_ARG, "null handle");
   if (!h->have_material) return fail(h, EP_ERR_STATE, "ep_apply_increment: set the material first");
   if (!(dt > 0.0)) return fail(h, EP_ERR_ARG, "ep_apply_increment: dt must be > 0");
@@ -580,37 +691,130 @@ static ep_status apply_common(ep_handle h, const double rates[3], double dt, con
   CK(h, cudaMemcpyAsync(h->dscal, &sc, sizeof(Scal), cudaMemcpyHostToDevice, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
   const size_t es = h->prec == EP_FP64 ? 8 : 4;
+  if (h->have_f != (body_force != nullptr) && h->chunk) {
+    cudaGraphExecDestroy(h->chunk);  // the captured kernels depend on the body force
+    h->chunk = nullptr;
+  }
   h->have_f = body_force != nullptr;
   size_t off = 0;
   int ex, ey, ez;
-  for (int d = 0; d < h->ndim; ++d) {
+  for (int d = 0; d < h->ndim && body_force; ++d) {
     field_extent(h, EP_VX + d, ex, ey, ez);
-    if (body_force) {
-      ep_status r = upload_box(h, body_force + off, h->Tn64[0], ex, ey, ez);
-      if (r != EP_OK) return r;
-      if (es == 8) CK(h, cudaMemcpyAsync(h->f[d], h->Tn64[0], h->g.box * 8, cudaMemcpyDeviceToDevice, h->stream));
-      else launch_convert<float, double>((float *)h->f[d], h->Tn64[0], h->g.box, h->stream);
-    }
+    ep_status r = upload_box(h, body_force + off, h->Tn64[0], ex, ey, ez);
+    if (r != EP_OK) return r;
+    if (es == 8) CK(h, cudaMemcpyAsync(h->f[d], h->Tn64[0], h->g.box * 8, cudaMemcpyDeviceToDevice, h->stream));
+    else launch_convert<float, double>((float *)h->f[d], h->Tn64[0], h->g.box, h->stream);
     off += (size_t)ex * ey * ez;
   }
-  const double *dv[3] = {nullptr, nullptr, nullptr};
-  if (dv_start) {
-    // Tn64 is free until the prologue's trial stage, which runs after the
-    // start-velocity kernel has consumed dv
-    off = 0;
-    for (int d = 0; d < h->ndim; ++d) {
-      field_extent(h, EP_VX + d, ex, ey, ez);
-      ep_status r = upload_box(h, dv_start + off, h->Tn64[d], ex, ey, ez);
-      if (r != EP_OK) return r;
-      dv[d] = h->Tn64[d];
-      off += (size_t)ex * ey * ez;
-    }
-  }
+  return EP_OK;
+}
+
+static ep_status run_prologue(ep_grid *h, const double *const dv[3]) {
   ep_status r = h->prec == EP_FP64 ? prologue<double>(h, dv) : prologue<float>(h, dv);
   if (r != EP_OK) return r;
   CK(h, cudaStreamSynchronize(h->stream));
   h->started = true;
   h->in_increment = true;
+  return EP_OK;
+}
+
+// start an increment whose start increment dv already lives on the device
+static ep_status apply_common_dev(ep_grid *h, const double rates[3], double dt, const double *body_force,
+                                  const double *const dv[3]) {
+  ep_status r = set_increment(h, rates, dt, body_force);
+  if (r != EP_OK) return r;
+  return run_prologue(h, dv);
+}
+
+// start an increment, with an optional host start increment dv_start
+static ep_status apply_common(ep_handle h, const double rates[3], double dt, const double *body_force,
+                              const double *dv_start) {
+  ep_status r = set_increment(h, rates, dt, body_force);
+  if (r != EP_OK) return r;
+  const double *dvh[3] = {nullptr, nullptr, nullptr};
+  if (dv_start) {
+    // Tn64 is free until the prologue's trial stage, which runs after the
+    // start-velocity kernel has consumed dv
+    size_t off = 0;
+    int ex, ey, ez;
+    for (int d = 0; d < h->ndim; ++d) {
+      field_extent(h, EP_VX + d, ex, ey, ez);
+      r = upload_box(h, dv_start + off, h->Tn64[d], ex, ey, ez);
+      if (r != EP_OK) return r;
+      dvh[d] = h->Tn64[d];
+      off += (size_t)ex * ey * ez;
+    }
+  }
+  return run_prologue(h, dvh);
+}
+
+static void warm_dims(const ep_grid *h, int dims[3]) {
+  dims[0] = (h->g.nx + 3) / 4 * 4;
+  dims[1] = (h->g.ny + 3) / 4 * 4;
+  dims[2] = h->ndim == 3 ? (h->g.nz + 3) / 4 * 4 : 1;
+}
+
+static ep_status warm_features_into(ep_grid *h, float *x) {
+  int dims[3];
+  warm_dims(h, dims);
+  launch_warm_scale(h->g, h->H, h->vpp, h->wscale, h->stream);
+  if (h->prec == EP_FP64) launch_warm_features<double>(h->g, h->H, h->vpp, P<double>(h->s), h->cmax, h->wscale, x, dims, h->stream);
+  else launch_warm_features<float>(h->g, h->H, h->vpp, P<float>(h->s), h->cmax, h->wscale, x, dims, h->stream);
+  CK(h, cudaGetLastError());
+  return EP_OK;
+}
+
+// start velocity from the network's prediction (device end to end)
+static ep_status apply_warm(ep_grid *h, const double rates[3], double dt, const double *body_force) {
+  int dims[3];
+  warm_dims(h, dims);
+  ep_status r = warm_features_into(h, h->wx);
+  if (r != EP_OK) return r;
+  CK(h, cudaStreamSynchronize(h->stream));
+  r = ep_net_forward(h->net, h->wx, 1, dims, h->wy);
+  if (r != EP_OK) return fail(h, r, std::string("warm start network: ") + ep_net_last_error(h->net));
+  CK(h, cudaDeviceSynchronize());
+  // Tn64 is free until the prologue's trial stage (after the start velocity)
+  double *dv[3] = {h->Tn64[0], h->Tn64[1], h->ndim == 3 ? h->Tn64[2] : nullptr};
+  launch_warm_dv(h->g, h->H, h->vpp, h->wy, h->wscale, dv, dims, h->stream);
+  CK(h, cudaGetLastError());
+  return apply_common_dev(h, rates, dt, body_force, dv);
+}
+
+ep_status ep_attach_warm_start(ep_handle h, ep_net_handle net) {
+  if (!h) return fail(nullptr, EP_ERR_ARG, "null handle");
+  if (h->wx) { cudaFree(h->wx); h->wx = nullptr; }
+  if (h->wy) { cudaFree(h->wy); h->wy = nullptr; }
+  h->net = net;
+  if (!net) return EP_OK;
+  int dims[3];
+  warm_dims(h, dims);
+  const long long nv = (long long)dims[0] * dims[1] * dims[2];
+  CK(h, cudaMalloc((void **)&h->wx, nv * (h->ndim + 2) * sizeof(float)));
+  CK(h, cudaMalloc((void **)&h->wy, nv * h->ndim * sizeof(float)));
+  return EP_OK;
+}
+
+ep_status ep_warm_features(ep_handle h, float *dev_out, double *scale, int dims[3]) {
+  if (!h || !dev_out) return fail(h, EP_ERR_ARG, "ep_warm_features: null argument");
+  if (h->n_commits < 2) return fail(h, EP_ERR_STATE, "ep_warm_features: needs two committed increments");
+  ep_status r = warm_features_into(h, dev_out);
+  if (r != EP_OK) return r;
+  unsigned long long b = 0;
+  CK(h, cudaMemcpyAsync(&b, h->wscale, sizeof(b), cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  if (scale) memcpy(scale, &b, sizeof(double));
+  if (dims) warm_dims(h, dims);
+  return EP_OK;
+}
+
+ep_status ep_warm_target(ep_handle h, const float *features, double scale, float *dev_out) {
+  if (!h || !features || !dev_out) return fail(h, EP_ERR_ARG, "ep_warm_target: null argument");
+  int dims[3];
+  warm_dims(h, dims);
+  launch_warm_target(h->g, h->H, h->vpp, features, scale, dev_out, dims, h->stream);
+  CK(h, cudaGetLastError());
+  CK(h, cudaStreamSynchronize(h->stream));
   return EP_OK;
 }
 
@@ -627,7 +831,8 @@ ep_status ep_apply_increment(ep_handle h, double a, double dt, int load_plane, c
   if (load_plane == EP_LOAD_XY) { r[0] = a; r[1] = -a; }
   else if (load_plane == EP_LOAD_XZ && h->ndim == 3) { r[0] = a; r[2] = -a; }
   else return fail(h, EP_ERR_ARG, "ep_apply_increment: load_plane must be EP_LOAD_XY, or EP_LOAD_XZ in 3D");
-  if (use_warm_start) return fail(h, EP_ERR_STATE, "ep_apply_increment: no warm-start predictor attached");
+  if (use_warm_start && !h->net) return fail(h, EP_ERR_STATE, "ep_apply_increment: no warm-start network attached");
+  if (use_warm_start && h->n_commits >= 2) return apply_warm(h, r, dt, body_force);
   return apply_common(h, r, dt, body_force, nullptr);
 }
 
@@ -760,6 +965,54 @@ ep_status ep_time_sweep(ep_handle h, int iters, double *ms_out, int n_out, int *
   std::vector<cudaEvent_t> ev(nk + 1);
   for (auto &e : ev) CK(h, cudaEventCreate(&e));
   std::vector<double> acc(nk + 1, 0.0);
+  const bool f2 = h->prec == EP_FP64 ? use_fused2d<double>(h) : use_fused2d<float>(h);
+  if (f2) {
+    ep_status r = h->prec == EP_FP64 ? prepare_solo2d<double>(h) : prepare_solo2d<float>(h);
+    if (r != EP_OK) return r;
+    const size_t el = h->prec == EP_FP64 ? 8 : 4;
+    const int blocks = std::min(persistent_blocks(h->tile, el), h->n_items);
+    for (int it = 0; it < iters; ++it) {
+      CK(h, cudaEventRecord(ev[0], h->stream));
+      if (el == 8)
+        launch_fused2d<double>(h->tile, (const Inst2<double> *)h->inst_dev, h->items_dev, h->n_items, it & 1, 0,
+                               blocks, h->stream);
+      else
+        launch_fused2d<float>(h->tile, (const Inst2<float> *)h->inst_dev, h->items_dev, h->n_items, it & 1, 0,
+                              blocks, h->stream);
+      CK(h, cudaEventRecord(ev[1], h->stream));
+      CK(h, cudaGetLastError());
+      CK(h, cudaEventSynchronize(ev[1]));
+      float ms = 0.f;
+      CK(h, cudaEventElapsedTime(&ms, ev[0], ev[1]));
+      acc[0] += ms;
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    ms_out[0] = acc[0] / iters;
+    if (n_out > 1) ms_out[1] = acc[0] / iters;
+    if (n_kernels) *n_kernels = 1;
+    h->in_increment = false;
+    return EP_OK;
+  }
+  const bool fused = h->prec == EP_FP64 ? use_fused<double>(h) : use_fused<float>(h);
+  if (fused) {
+    for (int it = 0; it < iters; ++it) {
+      CK(h, cudaEventRecord(ev[0], h->stream));
+      if (h->prec == EP_FP64) launch_fused3d<double>(h->g, sweep_stage<double>(h, it & 1), h->dscal, nullptr, h->kz, h->stream);
+      else launch_fused3d<float>(h->g, sweep_stage<float>(h, it & 1), h->dscal, nullptr, h->kz, h->stream);
+      CK(h, cudaEventRecord(ev[1], h->stream));
+      CK(h, cudaGetLastError());
+      CK(h, cudaEventSynchronize(ev[1]));
+      float ms = 0.f;
+      CK(h, cudaEventElapsedTime(&ms, ev[0], ev[1]));
+      acc[0] += ms;
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    ms_out[0] = acc[0] / iters;
+    if (n_out > 1) ms_out[1] = acc[0] / iters;
+    if (n_kernels) *n_kernels = 1;
+    h->in_increment = false;
+    return EP_OK;
+  }
   for (int it = 0; it < iters; ++it) {
     const int b = it & 1;
     CK(h, cudaEventRecord(ev[0], h->stream));
@@ -796,6 +1049,23 @@ ep_status ep_time_sweep(ep_handle h, int iters, double *ms_out, int n_out, int *
   return EP_OK;
 }
 
+ep_status ep_set_kernel(ep_handle h, int variant, int shape) {
+  if (!h) return fail(nullptr, EP_ERR_ARG, "null handle");
+  if (variant < EP_KERNEL_AUTO || variant > EP_KERNEL_FUSED)
+    return fail(h, EP_ERR_ARG, "ep_set_kernel: unknown variant");
+  if (shape >= 0 && ((h->ndim == 3 && shape < 1) || (h->ndim == 2 && shape > 2)))
+    return fail(h, EP_ERR_ARG, "ep_set_kernel: shape is z-planes >= 1 (3D) or a tile 0..2 (2D)");
+  if (h->chunk) {
+    cudaGraphExecDestroy(h->chunk);
+    h->chunk = nullptr;
+  }
+  h->variant = variant;
+  if (shape >= 0) {
+    if (h->ndim == 3) h->kz = shape; else h->tile = shape;
+  }
+  return EP_OK;
+}
+
 ep_status ep_sweep_bytes_per_cell(ep_handle h, double *bytes) {
   if (!h || !bytes) return fail(h, EP_ERR_ARG, "ep_sweep_bytes_per_cell: null argument");
   // reads: velocity increment (nd), stress state (nd + ns), pressure, base
@@ -804,6 +1074,244 @@ ep_status ep_sweep_bytes_per_cell(ep_handle h, double *bytes) {
   const int nd = h->ndim, ns = n_shear(nd);
   const double words = (nd + (nd + ns) + 1 + (nd + ns) + 1 + 1 + (ns + nd - 1)) + (nd + (nd + ns) + 1);
   *bytes = words * (h->prec == EP_FP64 ? 8.0 : 4.0);
+  return EP_OK;
+}
+
+}  // extern "C"
+
+struct ep_batch {
+  std::vector<ep_grid *> g;
+  int count = 0;
+  ep_precision prec = EP_FP64;
+  cudaStream_t stream = nullptr, cap = nullptr;
+  int tile = 0, blocks = 1, n_items = 0;
+  void *insts = nullptr;
+  int4 *items = nullptr;
+  DevInfo *dinfo = nullptr, *hinfo = nullptr;
+  cudaGraphExec_t chunk = nullptr;
+  double dt = 0.0;
+  std::vector<double> a;
+  std::string err;
+};
+
+static ep_status bfail(ep_batch *b, ep_status st, const std::string &m) {
+  if (b) b->err = m;
+  g_thread_err = m;
+  return st;
+}
+
+#define BCK(b, call)                                                                                \
+  do {                                                                                              \
+    cudaError_t e_ = (call);                                                                        \
+    if (e_ != cudaSuccess) return bfail((b), EP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+namespace {
+
+template <typename T>
+ep_status batch_upload(ep_batch *b) {
+  std::vector<Inst2<T>> I(b->count);
+  std::vector<int4> items;
+  for (int q = 0; q < b->count; ++q) {
+    I[q] = make_inst<T>(b->g[q], b->dinfo + q);
+    append_items(items, q, b->g[q]->g, b->tile);
+  }
+  if (b->items) cudaFree(b->items);
+  b->items = nullptr;
+  BCK(b, cudaMalloc((void **)&b->items, items.size() * sizeof(int4)));
+  BCK(b, cudaMemcpy(b->insts, I.data(), I.size() * sizeof(Inst2<T>), cudaMemcpyHostToDevice));
+  BCK(b, cudaMemcpy(b->items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  b->n_items = (int)items.size();
+  b->blocks = std::min(persistent_blocks(b->tile, sizeof(T)), b->n_items);
+  if (b->chunk) { cudaGraphExecDestroy(b->chunk); b->chunk = nullptr; }
+  return EP_OK;
+}
+
+template <typename T>
+ep_status batch_capture(ep_batch *b) {
+  if (b->chunk) return EP_OK;
+  cudaGraph_t graph;
+  const int nchk = b->g[0]->opts.n_chk;
+  BCK(b, cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+  for (int it = 0; it < nchk; ++it) {
+    launch_fused2d<T>(b->tile, (const Inst2<T> *)b->insts, b->items, b->n_items, it & 1, it == 0, b->blocks, b->cap);
+    if (it == 0) launch_check_batch<T>((const Inst2<T> *)b->insts, b->count, b->cap);
+  }
+  cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
+  if (e != cudaSuccess) return bfail(b, EP_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&b->chunk, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return bfail(b, EP_ERR_CUDA, std::string("batch instantiate: ") + cudaGetErrorString(e));
+  return EP_OK;
+}
+
+template <typename T>
+ep_status batch_solve(ep_batch *b, ep_solve_info *infos) {
+  ep_status r = batch_capture<T>(b);
+  if (r != EP_OK) return r;
+  cudaEvent_t e0, e1;
+  BCK(b, cudaEventCreate(&e0));
+  BCK(b, cudaEventCreate(&e1));
+  launch_init_batch<T>((const Inst2<T> *)b->insts, b->count, b->g[0]->opts.max_iter, b->stream);
+  BCK(b, cudaEventRecord(e0, b->stream));
+  const long long max_chunks = b->g[0]->opts.max_iter / b->g[0]->opts.n_chk + 2;
+  for (long long c = 0; c < max_chunks; ++c) {
+    BCK(b, cudaGraphLaunch(b->chunk, b->stream));
+    BCK(b, cudaMemcpyAsync(b->hinfo, b->dinfo, b->count * sizeof(DevInfo), cudaMemcpyDeviceToHost, b->stream));
+    BCK(b, cudaStreamSynchronize(b->stream));
+    bool all = true;
+    for (int q = 0; q < b->count; ++q) all = all && b->hinfo[q].done != 0;
+    if (all) break;
+  }
+  BCK(b, cudaEventRecord(e1, b->stream));
+  BCK(b, cudaEventSynchronize(e1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ep_status worst = EP_OK;
+  for (int q = 0; q < b->count; ++q) {
+    ep_grid *h = b->g[q];
+    const DevInfo di = b->hinfo[q];
+    ep_status st = di.done == 1 ? EP_OK : di.done == 2 ? EP_ERR_DIVERGED : EP_ERR_NOT_CONVERGED;
+    unsigned long long npl = 0;
+    double line[2] = {0, 0};
+    if (st == EP_OK) {
+      r = commit<T>(h);
+      if (r != EP_OK) return bfail(b, r, h->err);
+      BCK(b, cudaMemcpyAsync(&npl, h->dnpl, sizeof(npl), cudaMemcpyDeviceToHost, h->stream));
+      BCK(b, cudaMemcpyAsync(line, h->dline, sizeof(line), cudaMemcpyDeviceToHost, h->stream));
+      BCK(b, cudaStreamSynchronize(h->stream));
+    } else if (worst == EP_OK || st == EP_ERR_DIVERGED) {
+      worst = st;
+    }
+    if (infos) {
+      ep_solve_info &f = infos[q];
+      memset(&f, 0, sizeof(f));
+      f.iters = di.iters; f.eps_res = di.eps_res; f.eps_mom = di.eps_mom; f.eps_tau = di.eps_tau;
+      f.eps_p = di.eps_p; f.eps_rel = di.eps_rel; f.max_r = di.max_r; f.max_sigma = di.max_sig;
+      f.n_plastic = (long long)npl; f.sxx_int_centre = line[0]; f.sxx_int_right = line[1];
+      f.ms = ms; f.status = st;
+    }
+  }
+  if (worst != EP_OK) return bfail(b, worst, "some grids of the batch did not converge");
+  return EP_OK;
+}
+
+template <typename T>
+ep_status batch_restart(ep_batch *b) {
+  for (int q = 0; q < b->count; ++q) {
+    ep_grid *h = b->g[q];
+    h->in_increment = false;
+    ep_status r = apply_common(h, h->rate, b->dt, nullptr, nullptr);
+    if (r != EP_OK) return bfail(b, r, h->err);
+  }
+  return EP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ep_status ep_create_batch(const ep_handle *grids, int count, ep_batch_handle *out) {
+  if (!grids || count < 1 || !out) return bfail(nullptr, EP_ERR_ARG, "ep_create_batch: bad arguments");
+  *out = nullptr;
+  for (int q = 0; q < count; ++q) {
+    if (!grids[q] || grids[q]->ndim != 2) return bfail(nullptr, EP_ERR_ARG, "ep_create_batch: grids must be 2D");
+    if (grids[q]->prec != grids[0]->prec || grids[q]->opts.n_chk != grids[0]->opts.n_chk)
+      return bfail(nullptr, EP_ERR_ARG, "ep_create_batch: grids must share precision and n_chk");
+  }
+  ep_batch *b = new ep_batch();
+  b->count = count;
+  b->prec = grids[0]->prec;
+  b->stream = grids[0]->stream;
+  for (int q = 0; q < count; ++q) b->g.push_back(grids[q]);
+  const size_t isz = b->prec == EP_FP64 ? sizeof(Inst2<double>) : sizeof(Inst2<float>);
+  if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMalloc(&b->insts, isz * count) != cudaSuccess ||
+      cudaMalloc((void **)&b->dinfo, sizeof(DevInfo) * count) != cudaSuccess ||
+      cudaMallocHost((void **)&b->hinfo, sizeof(DevInfo) * count) != cudaSuccess) {
+    ep_destroy_batch(b);
+    return bfail(nullptr, EP_ERR_OOM, "ep_create_batch: allocation failed");
+  }
+  ep_status r = b->prec == EP_FP64 ? batch_upload<double>(b) : batch_upload<float>(b);
+  if (r != EP_OK) { ep_destroy_batch(b); return r; }
+  *out = b;
+  return EP_OK;
+}
+
+ep_status ep_batch_apply_increment(ep_batch_handle b, const double *a, double dt) {
+  if (!b || !a) return bfail(b, EP_ERR_ARG, "ep_batch_apply_increment: null argument");
+  b->dt = dt;
+  for (int q = 0; q < b->count; ++q) {
+    const double r[3] = {a[q], -a[q], 0.0};
+    ep_status st = apply_common(b->g[q], r, dt, nullptr, nullptr);
+    if (st != EP_OK) return bfail(b, st, b->g[q]->err);
+  }
+  return EP_OK;
+}
+
+ep_status ep_batch_solve_increment(ep_batch_handle b, ep_solve_info *infos) {
+  if (!b) return bfail(nullptr, EP_ERR_ARG, "null batch");
+  for (int q = 0; q < b->count; ++q)
+    if (!b->g[q]->in_increment) return bfail(b, EP_ERR_STATE, "ep_batch_solve_increment: apply an increment first");
+  return b->prec == EP_FP64 ? batch_solve<double>(b, infos) : batch_solve<float>(b, infos);
+}
+
+ep_status ep_batch_set_tile(ep_batch_handle b, int tile) {
+  if (!b || tile < 0 || tile > 2) return bfail(b, EP_ERR_ARG, "ep_batch_set_tile: tile must be 0..2");
+  b->tile = tile;
+  return b->prec == EP_FP64 ? batch_upload<double>(b) : batch_upload<float>(b);
+}
+
+ep_status ep_batch_autotune(ep_batch_handle b, int iters, int *tile_out) {
+  if (!b || iters < 1) return bfail(b, EP_ERR_ARG, "ep_batch_autotune: bad arguments");
+  for (int q = 0; q < b->count; ++q)
+    if (!b->g[q]->in_increment) return bfail(b, EP_ERR_STATE, "ep_batch_autotune: apply an increment first");
+  cudaEvent_t e0, e1;
+  BCK(b, cudaEventCreate(&e0));
+  BCK(b, cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_tile = 0;
+  for (int tile = 0; tile < 3; ++tile) {
+    b->tile = tile;
+    ep_status r = b->prec == EP_FP64 ? batch_upload<double>(b) : batch_upload<float>(b);
+    if (r != EP_OK) return r;
+    // one untimed sweep, then `iters` timed sweeps without checks
+    for (int it = 0; it <= iters; ++it) {
+      if (it == 1) BCK(b, cudaEventRecord(e0, b->stream));
+      if (b->prec == EP_FP64)
+        launch_fused2d<double>(tile, (const Inst2<double> *)b->insts, b->items, b->n_items, it & 1, 0, b->blocks, b->stream);
+      else
+        launch_fused2d<float>(tile, (const Inst2<float> *)b->insts, b->items, b->n_items, it & 1, 0, b->blocks, b->stream);
+    }
+    BCK(b, cudaEventRecord(e1, b->stream));
+    BCK(b, cudaEventSynchronize(e1));
+    BCK(b, cudaGetLastError());
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) { best = ms; best_tile = tile; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->tile = best_tile;
+  ep_status r = b->prec == EP_FP64 ? batch_upload<double>(b) : batch_upload<float>(b);
+  if (r != EP_OK) return r;
+  if (tile_out) *tile_out = best_tile;
+  // the timed sweeps advanced the iterates: start the increments again
+  return b->prec == EP_FP64 ? batch_restart<double>(b) : batch_restart<float>(b);
+}
+
+ep_status ep_destroy_batch(ep_batch_handle b) {
+  if (!b) return EP_OK;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->chunk) cudaGraphExecDestroy(b->chunk);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->insts) cudaFree(b->insts);
+  if (b->items) cudaFree(b->items);
+  if (b->dinfo) cudaFree(b->dinfo);
+  if (b->hinfo) cudaFreeHost(b->hinfo);
+  delete b;
   return EP_OK;
 }
 

@@ -83,6 +83,65 @@ struct Stage {
   int relax;                        // 1: sweep weights; 0: physical response
 };
 
+// One 2D instance of the batched fused sweep (ep_fused2d.cu): geometry,
+// scalars, convergence record and both ping-pong buffers of every array.
+template <typename T>
+struct Inst2 {
+  Geo g;
+  const Scal *sc;
+  DevInfo *di;
+  T *u[2][2];                       // [buffer][component]
+  T *sn[2][2], *ss[2], *sp[2];      // stress state: centres [buffer][comp], vertices, pressure
+  const T *tbn[2], *tbs, *pb, *yc, *rq, *rd;
+  T *s;
+  T *uchk[2], *cn[2], *cs, *cp;
+  const double *v0[2];
+};
+
+// Convergence decision after a check iteration (Eqs. Convergence1-3 in the
+// stopping measures described in ep_stages.cu).
+__device__ __forceinline__ void check_one(DevInfo *di, const Scal *sc) {
+  if (di->done) return;
+  auto bits = [](unsigned long long b) { return __longlong_as_double((long long)b); };
+  const double mr = bits(di->red[RED_R]), ms = bits(di->red[RED_SIG]);
+  const double dtau = bits(di->red[RED_DTAU]), dp = bits(di->red[RED_DP]);
+  const double du = bits(di->red[RED_DU]), vm = bits(di->red[RED_V]);
+  const double inf = __longlong_as_double(0x7ff0000000000000ll);
+  // iterations since the previous check (the start state for the first one)
+  const double m = di->k_check == 0 ? 1.0 : (double)sc->n_chk;
+  // momentum residual averaged over the interval: rho~ (u_{k+1} - u_chk) / m
+  double em = du == 0.0 ? 0.0 : (ms > 0.0 ? sc->dxmin * du / (m * sc->vstep) / ms : inf);
+  double et = dtau == 0.0 ? 0.0 : (ms > 0.0 ? dtau / (m * (1.0 - sc->bt)) / ms : inf);
+  double ep = dp == 0.0 ? 0.0 : (ms > 0.0 ? dp / (m * (1.0 - sc->bp)) / ms : inf);
+  double er = em > et ? em : et;
+  if (ep > er) er = ep;
+  if (isnan(em) || isnan(et) || isnan(ep) || isnan(ms) || isnan(du)) er = nan("");
+  const long long k = di->k_check;
+  di->iters = k;
+  di->eps_res = er; di->eps_mom = em; di->eps_tau = et; di->eps_p = ep;
+  di->eps_rel = vm > 0.0 ? du / vm : 0.0;
+  di->max_r = mr; di->max_sig = ms;
+  if (isnan(er) || isnan(mr) || isnan(du)) di->done = 2;
+  else if (er <= sc->tol) di->done = 1;
+  else if (k >= di->max_iter) di->done = 3;
+  else di->k_check = k + sc->n_chk;
+  for (int r = 0; r < RED_COUNT; ++r) di->red[r] = 0ull;
+}
+
+// ---- batched fused 2D sweep (ep_fused2d.cu) -------------------------------
+// tile: 0 = 32x8, 1 = 32x16, 2 = 64x8 cells
+template <typename T>
+void launch_fused2d(int tile, const Inst2<T> *insts, const int4 *items, int n_items, int b, int check, int blocks,
+                    cudaStream_t st);
+template <typename T>
+void launch_check_batch(const Inst2<T> *insts, int n, cudaStream_t st);
+template <typename T>
+void launch_init_batch(const Inst2<T> *insts, int n, long long max_iter, cudaStream_t st);
+void fused2d_tile(int tile, int *tx, int *ty);
+cudaError_t fused2d_configure();
+template <typename T>
+int fused2d_blocks_per_sm(int tile);
+
 // ---- staged sweep (one kernel per stage; ep_stages.cu) --------------------
 template <typename T>
 void launch_strain(const Geo &g, const Stage<T> &S, const Scal *sc, DevInfo *di, cudaStream_t st);
@@ -98,6 +157,13 @@ template <typename T>
 void launch_velocity(const Geo &g, const Stage<T> &S, const Scal *sc, DevInfo *di, int check,
                      cudaStream_t st);
 void launch_check(DevInfo *di, const Scal *sc, cudaStream_t st);
+
+// ---- fused sweeps (ep_fused3d.cu) ------------------------------------
+template <typename T>
+size_t fused3d_smem_bytes();
+cudaError_t fused3d_configure();
+template <typename T>
+void launch_fused3d(const Geo &g, const Stage<T> &S, const Scal *sc, const DevInfo *di, int kz, cudaStream_t st);
 
 // ---- increment set-up and commit (FP64; ep_increment.cu) ------------------
 struct History {
@@ -119,6 +185,15 @@ template <typename Td, typename Ts>
 void launch_convert(Td *dst, const Ts *src, long long n, cudaStream_t st);
 void launch_line_integrals(const Geo &g, const History &H, double *out2, cudaStream_t st);
 void launch_pack(const double *box, double *dst, int ex, int ey, int ez, int px, int py, cudaStream_t st);
+void launch_warm_scale(const Geo &g, const History &H, const double *const vp[3], unsigned long long *slot,
+                       cudaStream_t st);
+template <typename T>
+void launch_warm_features(const Geo &g, const History &H, const double *const vp[3], const T *s_last, double cmax,
+                          const unsigned long long *slot, float *x, const int dims[3], cudaStream_t st);
+void launch_warm_target(const Geo &g, const History &H, const double *const vp[3], const float *feat, double S,
+                        float *out, const int dims[3], cudaStream_t st);
+void launch_warm_dv(const Geo &g, const History &H, const double *const vp[3], const float *y,
+                    const unsigned long long *slot, double *const dv[3], const int dims[3], cudaStream_t st);
 void launch_unpack(const double *src, double *box, int ex, int ey, int ez, int px, int py, cudaStream_t st);
 
 }  // namespace ep

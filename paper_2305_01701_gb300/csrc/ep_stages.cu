@@ -10,7 +10,9 @@
 //              (check iterations also measure the stress change since the
 //              previous check, for the pseudo-time residuals)
 //   edges    : edge deviator = mean of the adjacent centre scales x T
-//   velocity : momentum residual (Eq. A22S) and u += R / rho~ (Eq. A22P)
+//   velocity : momentum residual (Eq. A22S) and u += R / rho~ (Eq. A22P);
+//              check iterations measure the change of u since the previous
+//              check (the interval-averaged momentum residual)
 // Every quantity is computed exactly once per iteration (no halo
 // recomputation), which is what an FP64-bound sweep on GB300 wants.  The
 // same kernels with beta = 0 evaluate the physical response for the FP64
@@ -345,9 +347,9 @@ __global__ void __launch_bounds__(kThreads) k_velocity(Geo g, Stage<T> S, const 
       }
       S.uo[0][e] = un;
       if (check) {
-        du = fabs((double)u - (double)S.uchk[0][e]);
+        du = fabs((double)un - (double)S.uchk[0][e]);
         vm = fabs(S.v0[0][e] + (double)u);
-        S.uchk[0][e] = u;
+        S.uchk[0][e] = un;
       }
     } else {
       S.uo[0][e] = S.u[0][e];
@@ -365,9 +367,9 @@ __global__ void __launch_bounds__(kThreads) k_velocity(Geo g, Stage<T> S, const 
       }
       S.uo[1][e] = un;
       if (check) {
-        du = maxn(du, fabs((double)u - (double)S.uchk[1][e]));
+        du = maxn(du, fabs((double)un - (double)S.uchk[1][e]));
         vm = maxn(vm, fabs(S.v0[1][e] + (double)u));
-        S.uchk[1][e] = u;
+        S.uchk[1][e] = un;
       }
     } else {
       S.uo[1][e] = S.u[1][e];
@@ -385,9 +387,9 @@ __global__ void __launch_bounds__(kThreads) k_velocity(Geo g, Stage<T> S, const 
         }
         S.uo[2][e] = un;
         if (check) {
-          du = maxn(du, fabs((double)u - (double)S.uchk[2][e]));
+          du = maxn(du, fabs((double)un - (double)S.uchk[2][e]));
           vm = maxn(vm, fabs(S.v0[2][e] + (double)u));
-          S.uchk[2][e] = u;
+          S.uchk[2][e] = un;
         }
       } else {
         S.uo[2][e] = S.u[2][e];
@@ -401,34 +403,11 @@ __global__ void __launch_bounds__(kThreads) k_velocity(Geo g, Stage<T> S, const 
   }
 }
 
-__device__ __forceinline__ double from_bits(unsigned long long b) { return __longlong_as_double((long long)b); }
 
 // Convergence decision after a check iteration (Sec. 4.2 measures).
 __global__ void k_check(DevInfo *di, const Scal *sc) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  if (di->done) return;
-  const double mr = from_bits(di->red[RED_R]), ms = from_bits(di->red[RED_SIG]);
-  const double dtau = from_bits(di->red[RED_DTAU]), dp = from_bits(di->red[RED_DP]);
-  const double du = from_bits(di->red[RED_DU]), vm = from_bits(di->red[RED_V]);
-  const double inf = __longlong_as_double(0x7ff0000000000000ll);
-  // iterations since the previous check (the start state for the first one)
-  const double m = di->k_check == 0 ? 1.0 : (double)sc->n_chk;
-  double em = mr == 0.0 ? 0.0 : (ms > 0.0 ? sc->dxmin * mr / ms : inf);
-  double et = dtau == 0.0 ? 0.0 : (ms > 0.0 ? dtau / (m * (1.0 - sc->bt)) / ms : inf);
-  double ep = dp == 0.0 ? 0.0 : (ms > 0.0 ? dp / (m * (1.0 - sc->bp)) / ms : inf);
-  double er = em > et ? em : et;
-  if (ep > er) er = ep;
-  if (isnan(em) || isnan(et) || isnan(ep) || isnan(ms)) er = nan("");
-  const long long k = di->k_check;
-  di->iters = k;
-  di->eps_res = er; di->eps_mom = em; di->eps_tau = et; di->eps_p = ep;
-  di->eps_rel = vm > 0.0 ? du / vm : 0.0;
-  di->max_r = mr; di->max_sig = ms;
-  if (isnan(er) || isnan(mr)) di->done = 2;
-  else if (er <= sc->tol) di->done = 1;
-  else if (k >= di->max_iter) di->done = 3;
-  else di->k_check = k + sc->n_chk;
-  for (int r = 0; r < RED_COUNT; ++r) di->red[r] = 0ull;
+  check_one(di, sc);
 }
 
 inline unsigned blocks_for(long long n) { return (unsigned)((n + kThreads - 1) / kThreads); }

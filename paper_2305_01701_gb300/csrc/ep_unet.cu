@@ -1,0 +1,687 @@
+// ep_unet.cu -- the learned warm start: a small convolutional U-Net that
+// predicts an increment's velocity change from the previous increments, with
+// hand-written forward, backward and optimiser kernels.
+//
+// Network (D = 2 or 3 spatial dimensions, activations NC[Z]YX in FP32,
+// weights BF16 with FP32 master copies):
+//   level l = 0..L-1 : conv3(c_{l-1} -> c_l) + ReLU, conv3(c_l -> c_l) + ReLU
+//                      (c_l = base * 2^l), average-pool by 2 between levels;
+//   decoder          : nearest upsample, concatenate the skip of the same
+//                      level, two conv3 + ReLU;
+//   head             : conv1 (c_0 -> out), no activation, zero-initialised.
+// The prediction is added to a baseline chosen by the caller (the previous
+// increment's velocity change), so an untrained network reproduces it.
+// Training: MSE loss, Adam.  The convolutions run on CUDA cores with FP32
+// accumulation: at the sizes used (<= 128 channels) they are a small part of
+// an increment's solve time.
+#include <cuda_bf16.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "ep_internal.cuh"
+
+namespace ep {
+
+namespace {
+
+constexpr int NT = 256;
+
+inline unsigned nblk(long long n) { return (unsigned)((n + NT - 1) / NT); }
+
+// ---- direct convolution (3^D or 1^D taps), zero padding -------------------
+// y[n, co, p] = b[co] + sum_{ci, tap} W(co, ci, tap) x[n, ci, p + tap - r]
+// TRANS = true computes the data gradient: channels swapped and taps
+// mirrored, i.e. dx = conv(dy, W^T flipped); then b is unused.
+template <int D, int K, bool TRANS>
+__global__ void k_conv(const float *__restrict__ x, const __nv_bfloat16 *__restrict__ w, const float *__restrict__ b,
+                       float *__restrict__ y, int N, int cin, int cout, int X, int Y, int Z, int relu,
+                       int w_cin, int w_cout) {
+  // one thread per output voxel, a chunk of 8 output channels per blockIdx.y
+  constexpr int CB = 8;
+  constexpr int R = K / 2;
+  const long long nvox = (long long)X * Y * Z;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int co0 = blockIdx.y * CB;
+  const int n = blockIdx.z;
+  if (t >= nvox) return;
+  const int ix = (int)(t % X), iy = (int)((t / X) % Y), iz = (int)(t / ((long long)X * Y));
+  float acc[CB];
+#pragma unroll
+  for (int c = 0; c < CB; ++c) acc[c] = (!TRANS && b && co0 + c < cout) ? b[co0 + c] : 0.f;
+  const float *xn = x + (long long)n * cin * nvox;
+  constexpr int KZ = D == 3 ? K : 1;
+  for (int ci = 0; ci < cin; ++ci) {
+    const float *xc = xn + (long long)ci * nvox;
+    for (int dz = 0; dz < KZ; ++dz) {
+      const int zz = D == 3 ? iz + dz - R : iz;
+      if (zz < 0 || zz >= Z) continue;
+      for (int dy = 0; dy < K; ++dy) {
+        const int yy = iy + dy - R;
+        if (yy < 0 || yy >= Y) continue;
+        for (int dx = 0; dx < K; ++dx) {
+          const int xx = ix + dx - R;
+          if (xx < 0 || xx >= X) continue;
+          const float v = xc[((long long)zz * Y + yy) * X + xx];
+          const int tap = (dz * K + dy) * K + dx;
+          const int taps = KZ * K * K;
+#pragma unroll
+          for (int c = 0; c < CB; ++c) {
+            const int co = co0 + c;
+            if (co >= cout) break;
+            // forward: W[co][ci][tap]; transposed: W[ci'=co_out... ] mirrored
+            long long wi;
+            if (!TRANS) wi = ((long long)co * w_cin + ci) * taps + tap;
+            else wi = ((long long)ci * w_cin + co) * taps + (taps - 1 - tap);
+            acc[c] += __bfloat162float(w[wi]) * v;
+          }
+        }
+      }
+    }
+  }
+  float *yn = y + (long long)n * cout * nvox;
+#pragma unroll
+  for (int c = 0; c < CB; ++c) {
+    const int co = co0 + c;
+    if (co >= cout) break;
+    float v = acc[c];
+    if (relu && v < 0.f) v = 0.f;
+    yn[(long long)co * nvox + t] = v;
+  }
+}
+
+// weight gradient: dW[co][ci][tap] += sum_{n, p} dy[n, co, p] x[n, ci, p + tap - r]
+// one block per (co, ci); threads stride over voxels, block-reduce per tap.
+template <int D, int K>
+__global__ void k_conv_wgrad(const float *__restrict__ x, const float *__restrict__ dy, float *__restrict__ dw,
+                             float *__restrict__ db, int N, int cin, int cout, int X, int Y, int Z) {
+  constexpr int R = K / 2, KZ = D == 3 ? K : 1, TAPS = KZ * K * K;
+  const int co = blockIdx.x, ci = blockIdx.y;
+  const long long nvox = (long long)X * Y * Z;
+  float acc[TAPS];
+#pragma unroll
+  for (int q = 0; q < TAPS; ++q) acc[q] = 0.f;
+  float accb = 0.f;
+  for (int n = 0; n < N; ++n) {
+    const float *g = dy + ((long long)n * cout + co) * nvox;
+    const float *xc = x + ((long long)n * cin + ci) * nvox;
+    for (long long t = threadIdx.x; t < nvox; t += blockDim.x) {
+      const float gv = g[t];
+      if (gv == 0.f) continue;
+      const int ix = (int)(t % X), iy = (int)((t / X) % Y), iz = (int)(t / ((long long)X * Y));
+      if (ci == 0) accb += gv;
+#pragma unroll
+      for (int dz = 0; dz < KZ; ++dz) {
+        const int zz = D == 3 ? iz + dz - R : iz;
+#pragma unroll
+        for (int dyy = 0; dyy < K; ++dyy) {
+          const int yy = iy + dyy - R;
+#pragma unroll
+          for (int dx = 0; dx < K; ++dx) {
+            const int xx = ix + dx - R;
+            const bool ok = xx >= 0 && xx < X && yy >= 0 && yy < Y && zz >= 0 && zz < Z;
+            if (ok) acc[(dz * K + dyy) * K + dx] += gv * xc[((long long)zz * Y + yy) * X + xx];
+          }
+        }
+      }
+    }
+  }
+  __shared__ float red[NT / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int q = 0; q <= TAPS; ++q) {
+    float v = q < TAPS ? acc[q] : accb;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float s = 0.f;
+      for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) s += red[w2];
+      if (q < TAPS) dw[((long long)co * cin + ci) * TAPS + q] += s;
+      else if (ci == 0 && db) db[co] += s;
+    }
+  }
+}
+
+__global__ void k_relu_bwd(const float *a, float *g, long long n) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n && a[t] <= 0.f) g[t] = 0.f;
+}
+
+// average pool by 2 in every spatial dimension (sizes are even)
+template <int D>
+__global__ void k_pool(const float *x, float *y, long long NC, int X, int Y, int Z) {
+  const int x2 = X / 2, y2 = Y / 2, z2 = D == 3 ? Z / 2 : 1;
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long nv = (long long)x2 * y2 * z2;
+  if (t >= NC * nv) return;
+  long long c = t / nv, v = t % nv;
+  int ix = (int)(v % x2), iy = (int)((v / x2) % y2), iz = (int)(v / ((long long)x2 * y2));
+  const float *xc = x + c * (long long)X * Y * Z;
+  float s = 0.f;
+  for (int dz = 0; dz < (D == 3 ? 2 : 1); ++dz)
+    for (int dy = 0; dy < 2; ++dy)
+      for (int dx = 0; dx < 2; ++dx)
+        s += xc[((long long)(D == 3 ? 2 * iz + dz : 0) * Y + 2 * iy + dy) * X + 2 * ix + dx];
+  y[t] = s * (D == 3 ? 0.125f : 0.25f);
+}
+
+template <int D>
+__global__ void k_pool_bwd(const float *gy, float *gx, long long NC, int X, int Y, int Z) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long nv = (long long)X * Y * Z;
+  if (t >= NC * nv) return;
+  long long c = t / nv, v = t % nv;
+  int ix = (int)(v % X), iy = (int)((v / X) % Y), iz = (int)(v / ((long long)X * Y));
+  const int x2 = X / 2, y2 = Y / 2;
+  const long long n2 = (long long)x2 * y2 * (D == 3 ? Z / 2 : 1);
+  gx[t] = gy[c * n2 + ((long long)(D == 3 ? iz / 2 : 0) * y2 + iy / 2) * x2 + ix / 2] * (D == 3 ? 0.125f : 0.25f);
+}
+
+// nearest upsample by 2 into channel slot [c_off, c_off + C) of a wider tensor
+template <int D>
+__global__ void k_up(const float *x, float *y, int N, int C, int ctot, int c_off, int X, int Y, int Z) {
+  // X, Y, Z: sizes of the (fine) output
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long nv = (long long)X * Y * Z;
+  if (t >= (long long)N * C * nv) return;
+  long long nc = t / nv, v = t % nv;
+  int n = (int)(nc / C), c = (int)(nc % C);
+  int ix = (int)(v % X), iy = (int)((v / X) % Y), iz = (int)(v / ((long long)X * Y));
+  const int x2 = X / 2, y2 = Y / 2;
+  const long long n2 = (long long)x2 * y2 * (D == 3 ? Z / 2 : 1);
+  y[((long long)n * ctot + c_off + c) * nv + v] =
+      x[((long long)n * C + c) * n2 + ((long long)(D == 3 ? iz / 2 : 0) * y2 + iy / 2) * x2 + ix / 2];
+}
+
+template <int D>
+__global__ void k_up_bwd(const float *gy, float *gx, int N, int C, int ctot, int c_off, int X, int Y, int Z) {
+  // gx: coarse (X/2...), gy: fine slot
+  const int x2 = X / 2, y2 = Y / 2, z2 = D == 3 ? Z / 2 : 1;
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long n2 = (long long)x2 * y2 * z2, nv = (long long)X * Y * Z;
+  if (t >= (long long)N * C * n2) return;
+  long long nc = t / n2, v = t % n2;
+  int n = (int)(nc / C), c = (int)(nc % C);
+  int ix = (int)(v % x2), iy = (int)((v / x2) % y2), iz = (int)(v / ((long long)x2 * y2));
+  const float *g = gy + ((long long)n * ctot + c_off + c) * nv;
+  float s = 0.f;
+  for (int dz = 0; dz < (D == 3 ? 2 : 1); ++dz)
+    for (int dy = 0; dy < 2; ++dy)
+      for (int dx = 0; dx < 2; ++dx)
+        s += g[((long long)(D == 3 ? 2 * iz + dz : 0) * Y + 2 * iy + dy) * X + 2 * ix + dx];
+  gx[t] = s;
+}
+
+// copy channels [0, C) of a tensor into slot [c_off, c_off + C) of a wider one (and back)
+__global__ void k_slot_copy(const float *src, float *dst, int N, int C, int csrc, int soff, int cdst, int doff,
+                            long long nv, int accumulate) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)N * C * nv) return;
+  long long nc = t / nv, v = t % nv;
+  int n = (int)(nc / C), c = (int)(nc % C);
+  float val = src[((long long)n * csrc + soff + c) * nv + v];
+  float *d = dst + ((long long)n * cdst + doff + c) * nv + v;
+  if (accumulate) *d += val; else *d = val;
+}
+
+// MSE loss between y and target (both N x C x nv): grad = 2 (y - t) / count
+__global__ void k_mse(const float *y, const float *t, float *g, long long n, double *loss) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double d2 = 0.0;
+  if (i < n) {
+    float d = y[i] - t[i];
+    g[i] = 2.f * d / (float)n;
+    d2 = (double)d * d;
+  }
+  for (int o = 16; o > 0; o >>= 1) d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+  if ((threadIdx.x & 31) == 0 && d2 != 0.0) atomicAdd(loss, d2 / (double)n);
+}
+
+__global__ void k_adam(float *w, __nv_bfloat16 *wb, const float *g, float *m, float *v, long long n, float lr,
+                       float b1, float b2, float eps, float c1, float c2) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float gi = g[i];
+  float mi = b1 * m[i] + (1.f - b1) * gi;
+  float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  w[i] = wi;
+  wb[i] = __float2bfloat16_rn(wi);
+}
+
+__global__ void k_to_bf16(const float *w, __nv_bfloat16 *wb, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) wb[i] = __float2bfloat16_rn(w[i]);
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------------------
+struct Layer {
+  int cin, cout, k;
+  long long woff, boff;   // offsets into the parameter vector
+};
+
+struct UNet {
+  int D, cin, cout, base, levels;
+  std::vector<Layer> layers;  // enc (2 per level), dec (2 per level except last), head
+  long long nparam = 0;
+  float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
+  __nv_bfloat16 *wb = nullptr;
+  long long step = 0;
+  // activations for the current shape
+  int N = 0, X = 0, Y = 0, Z = 0;
+  std::vector<float *> act, grad;   // per stored tensor
+  std::vector<int> act_c;           // channels of each stored tensor
+  std::vector<int> act_lvl;         // level (resolution) of each stored tensor
+  float *scratch = nullptr, *scratch2 = nullptr;
+  long long scratch_n = 0;
+  double *dloss = nullptr;
+  cudaStream_t st = nullptr;
+};
+
+static long long vox(const UNet &u, int lvl) {
+  long long s = 1;
+  s *= (u.X >> lvl);
+  s *= (u.Y >> lvl);
+  if (u.D == 3) s *= (u.Z >> lvl);
+  return s;
+}
+
+// Build the layer table and parameter offsets.
+static void unet_layers(UNet &u) {
+  long long off = 0;
+  auto add = [&](int ci, int co, int k) {
+    Layer L{ci, co, k, off, 0};
+    long long taps = (long long)k * k * (u.D == 3 ? k : 1);
+    off += (long long)ci * co * taps;
+    L.boff = off;
+    off += co;
+    u.layers.push_back(L);
+  };
+  int c_prev = u.cin;
+  for (int l = 0; l < u.levels; ++l) {
+    int c = u.base << l;
+    add(c_prev, c, 3);
+    add(c, c, 3);
+    c_prev = c;
+  }
+  for (int l = u.levels - 2; l >= 0; --l) {
+    int c = u.base << l, cup = u.base << (l + 1);
+    add(cup + c, c, 3);
+    add(c, c, 3);
+  }
+  add(u.base, u.cout, 1);
+  u.nparam = off;
+}
+
+}  // namespace ep
+
+namespace ep {
+
+static cudaError_t ensure_shape(UNet &u, int N, int X, int Y, int Z) {
+  if (u.N == N && u.X == X && u.Y == Y && u.Z == Z) return cudaSuccess;
+  for (float *p : u.act) cudaFree(p);
+  for (float *p : u.grad) cudaFree(p);
+  u.act.clear(); u.grad.clear(); u.act_c.clear(); u.act_lvl.clear();
+  if (u.scratch) cudaFree(u.scratch);
+  if (u.scratch2) cudaFree(u.scratch2);
+  u.scratch = u.scratch2 = nullptr;
+  u.N = N; u.X = X; u.Y = Y; u.Z = Z;
+  // tensors in forward order: e[l][0], e[l][1], pool[l] (l < L-1), then per
+  // decoder level: cat, d0, d1; then the head output
+  auto add = [&](int c, int lvl) {
+    float *a = nullptr, *g = nullptr;
+    size_t bytes = (size_t)N * c * vox(u, lvl) * sizeof(float);
+    cudaError_t e = cudaMalloc((void **)&a, bytes);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&g, bytes);
+    u.act.push_back(a); u.grad.push_back(g); u.act_c.push_back(c); u.act_lvl.push_back(lvl);
+    return e;
+  };
+  cudaError_t e = cudaSuccess;
+  for (int l = 0; l < u.levels && e == cudaSuccess; ++l) {
+    int c = u.base << l;
+    e = add(c, l);
+    if (e == cudaSuccess) e = add(c, l);
+    if (e == cudaSuccess && l < u.levels - 1) e = add(c, l + 1);
+  }
+  for (int l = u.levels - 2; l >= 0 && e == cudaSuccess; --l) {
+    int c = u.base << l, cup = u.base << (l + 1);
+    e = add(cup + c, l);
+    if (e == cudaSuccess) e = add(c, l);
+    if (e == cudaSuccess) e = add(c, l);
+  }
+  if (e == cudaSuccess) e = add(u.cout, 0);
+  long long big = (long long)N * (u.base << (u.levels - 1)) * 2 * vox(u, 0);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&u.scratch, big * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&u.scratch2, big * sizeof(float));
+  u.scratch_n = big;
+  return e;
+}
+
+// tensor indices of the forward graph
+struct Idx {
+  int e0[8], e1[8], pool[8], cat[8], d0[8], d1[8], out;
+};
+static Idx indices(const UNet &u) {
+  Idx I{};
+  int q = 0;
+  for (int l = 0; l < u.levels; ++l) {
+    I.e0[l] = q++;
+    I.e1[l] = q++;
+    if (l < u.levels - 1) I.pool[l] = q++;
+  }
+  for (int l = u.levels - 2; l >= 0; --l) {
+    I.cat[l] = q++;
+    I.d0[l] = q++;
+    I.d1[l] = q++;
+  }
+  I.out = q++;
+  return I;
+}
+
+template <int D>
+static void conv_fwd(UNet &u, const Layer &L, const float *x, float *y, int lvl, int relu) {
+  const long long nv = vox(u, lvl);
+  dim3 grid(nblk(nv), (L.cout + 7) / 8, u.N);
+  const int X = u.X >> lvl, Y = u.Y >> lvl, Z = D == 3 ? (u.Z >> lvl) : 1;
+  if (L.k == 3)
+    k_conv<D, 3, false><<<grid, NT, 0, u.st>>>(x, u.wb + L.woff, u.w + L.boff, y, u.N, L.cin, L.cout, X, Y, Z, relu,
+                                               L.cin, L.cout);
+  else
+    k_conv<D, 1, false><<<grid, NT, 0, u.st>>>(x, u.wb + L.woff, u.w + L.boff, y, u.N, L.cin, L.cout, X, Y, Z, relu,
+                                               L.cin, L.cout);
+}
+
+// data gradient gx (cin channels) from gy (cout channels); weight gradient into u.g
+template <int D>
+static void conv_bwd(UNet &u, const Layer &L, const float *x, const float *gy, float *gx, int lvl) {
+  const long long nv = vox(u, lvl);
+  const int X = u.X >> lvl, Y = u.Y >> lvl, Z = D == 3 ? (u.Z >> lvl) : 1;
+  dim3 wg(L.cout, L.cin);
+  if (L.k == 3) k_conv_wgrad<D, 3><<<wg, NT, 0, u.st>>>(x, gy, u.g + L.woff, u.g + L.boff, u.N, L.cin, L.cout, X, Y, Z);
+  else k_conv_wgrad<D, 1><<<wg, NT, 0, u.st>>>(x, gy, u.g + L.woff, u.g + L.boff, u.N, L.cin, L.cout, X, Y, Z);
+  if (!gx) return;
+  dim3 grid(nblk(nv), (L.cin + 7) / 8, u.N);
+  if (L.k == 3)
+    k_conv<D, 3, true><<<grid, NT, 0, u.st>>>(gy, u.wb + L.woff, nullptr, gx, u.N, L.cout, L.cin, X, Y, Z, 0, L.cin,
+                                              L.cout);
+  else
+    k_conv<D, 1, true><<<grid, NT, 0, u.st>>>(gy, u.wb + L.woff, nullptr, gx, u.N, L.cout, L.cin, X, Y, Z, 0, L.cin,
+                                              L.cout);
+}
+
+static void relu_bwd(UNet &u, int q) {
+  long long n = (long long)u.N * u.act_c[q] * vox(u, u.act_lvl[q]);
+  k_relu_bwd<<<nblk(n), NT, 0, u.st>>>(u.act[q], u.grad[q], n);
+}
+
+template <int D>
+static void forward(UNet &u, const float *x) {
+  const Idx I = indices(u);
+  int li = 0;
+  const float *in = x;
+  for (int l = 0; l < u.levels; ++l) {
+    conv_fwd<D>(u, u.layers[li++], in, u.act[I.e0[l]], l, 1);
+    conv_fwd<D>(u, u.layers[li++], u.act[I.e0[l]], u.act[I.e1[l]], l, 1);
+    if (l < u.levels - 1) {
+      const int X = u.X >> l, Y = u.Y >> l, Z = D == 3 ? (u.Z >> l) : 1;
+      long long n = (long long)u.N * u.act_c[I.pool[l]] * vox(u, l + 1);
+      k_pool<D><<<nblk(n), NT, 0, u.st>>>(u.act[I.e1[l]], u.act[I.pool[l]], (long long)u.N * (u.base << l), X, Y, Z);
+      in = u.act[I.pool[l]];
+    }
+  }
+  const float *prev = u.act[I.e1[u.levels - 1]];
+  for (int l = u.levels - 2; l >= 0; --l) {
+    const int c = u.base << l, cup = u.base << (l + 1);
+    const int X = u.X >> l, Y = u.Y >> l, Z = D == 3 ? (u.Z >> l) : 1;
+    const long long nv = vox(u, l);
+    k_up<D><<<nblk((long long)u.N * cup * nv), NT, 0, u.st>>>(prev, u.act[I.cat[l]], u.N, cup, cup + c, 0, X, Y, Z);
+    k_slot_copy<<<nblk((long long)u.N * c * nv), NT, 0, u.st>>>(u.act[I.e1[l]], u.act[I.cat[l]], u.N, c, c, 0,
+                                                                cup + c, cup, nv, 0);
+    conv_fwd<D>(u, u.layers[li++], u.act[I.cat[l]], u.act[I.d0[l]], l, 1);
+    conv_fwd<D>(u, u.layers[li++], u.act[I.d0[l]], u.act[I.d1[l]], l, 1);
+    prev = u.act[I.d1[l]];
+  }
+  conv_fwd<D>(u, u.layers[li++], prev, u.act[I.out], 0, 0);
+}
+
+// gradients of all parameters given d loss / d out in u.grad[out]
+template <int D>
+static void backward(UNet &u, const float *x) {
+  const Idx I = indices(u);
+  const int nl = (int)u.layers.size();
+  int li = nl - 1;
+  // zero the activation gradients that are accumulated into: every e1 (skip
+  // and pool/up paths) and the decoder outputs below the finest level (their
+  // only contribution arrives through the upsampling of the next finer level)
+  for (int l = 0; l < u.levels; ++l) {
+    long long n = (long long)u.N * u.act_c[I.e1[l]] * vox(u, l);
+    cudaMemsetAsync(u.grad[I.e1[l]], 0, n * sizeof(float), u.st);
+  }
+  for (int l = 1; l <= u.levels - 2; ++l) {
+    long long n = (long long)u.N * u.act_c[I.d1[l]] * vox(u, l);
+    cudaMemsetAsync(u.grad[I.d1[l]], 0, n * sizeof(float), u.st);
+  }
+  const int top = u.levels == 1 ? I.e1[0] : I.d1[0];
+  // head
+  {
+    long long n = (long long)u.N * u.base * vox(u, 0);
+    if (u.levels == 1) {
+      conv_bwd<D>(u, u.layers[li--], u.act[top], u.grad[I.out], u.scratch, 0);
+      k_slot_copy<<<nblk(n), NT, 0, u.st>>>(u.scratch, u.grad[top], u.N, u.base, u.base, 0, u.base, 0, vox(u, 0), 1);
+    } else {
+      conv_bwd<D>(u, u.layers[li--], u.act[top], u.grad[I.out], u.grad[top], 0);
+    }
+  }
+  // decoder, finest level first
+  for (int l = 0; l <= u.levels - 2; ++l) {
+    const int c = u.base << l, cup = u.base << (l + 1);
+    const int X = u.X >> l, Y = u.Y >> l, Z = D == 3 ? (u.Z >> l) : 1;
+    const long long nv = vox(u, l);
+    const Layer &L1 = u.layers[li--];
+    const Layer &L0 = u.layers[li--];
+    relu_bwd(u, I.d1[l]);
+    conv_bwd<D>(u, L1, u.act[I.d0[l]], u.grad[I.d1[l]], u.grad[I.d0[l]], l);
+    relu_bwd(u, I.d0[l]);
+    conv_bwd<D>(u, L0, u.act[I.cat[l]], u.grad[I.d0[l]], u.grad[I.cat[l]], l);
+    // split the concatenation: upsampled part -> coarser tensor, skip -> e1[l]
+    k_slot_copy<<<nblk((long long)u.N * c * nv), NT, 0, u.st>>>(u.grad[I.cat[l]], u.grad[I.e1[l]], u.N, c, cup + c,
+                                                                cup, c, 0, nv, 1);
+    const int coarse = l + 1 == u.levels - 1 ? I.e1[l + 1] : I.d1[l + 1];
+    const long long n2 = (long long)u.N * cup * vox(u, l + 1);
+    k_up_bwd<D><<<nblk(n2), NT, 0, u.st>>>(u.grad[I.cat[l]], u.scratch, u.N, cup, cup + c, 0, X, Y, Z);
+    k_slot_copy<<<nblk(n2), NT, 0, u.st>>>(u.scratch, u.grad[coarse], u.N, cup, cup, 0, cup, 0, vox(u, l + 1), 1);
+  }
+  // encoder, coarsest level first
+  for (int l = u.levels - 1; l >= 0; --l) {
+    const Layer &L1 = u.layers[2 * l + 1];
+    const Layer &L0 = u.layers[2 * l];
+    relu_bwd(u, I.e1[l]);
+    conv_bwd<D>(u, L1, u.act[I.e0[l]], u.grad[I.e1[l]], u.grad[I.e0[l]], l);
+    relu_bwd(u, I.e0[l]);
+    const float *in = l == 0 ? x : u.act[I.pool[l - 1]];
+    float *gin = l == 0 ? nullptr : u.grad[I.pool[l - 1]];
+    conv_bwd<D>(u, L0, in, u.grad[I.e0[l]], gin, l);
+    if (l > 0) {
+      const int X = u.X >> (l - 1), Y = u.Y >> (l - 1), Z = D == 3 ? (u.Z >> (l - 1)) : 1;
+      const int cl = u.base << (l - 1);
+      long long n = (long long)u.N * cl * vox(u, l - 1);
+      k_pool_bwd<D><<<nblk(n), NT, 0, u.st>>>(u.grad[I.pool[l - 1]], u.scratch, (long long)u.N * cl, X, Y, Z);
+      k_slot_copy<<<nblk(n), NT, 0, u.st>>>(u.scratch, u.grad[I.e1[l - 1]], u.N, cl, cl, 0, cl, 0, vox(u, l - 1), 1);
+    }
+  }
+}
+
+}  // namespace ep
+
+// ============================================================================
+using namespace ep;
+
+struct ep_net {
+  UNet u;
+  std::string err;
+};
+
+static thread_local std::string g_net_err;
+
+static ep_status nfail(ep_net *n, ep_status st, const std::string &m) {
+  if (n) n->err = m;
+  g_net_err = m;
+  return st;
+}
+
+#define NCK(n, call)                                                                                  \
+  do {                                                                                                \
+    cudaError_t e_ = (call);                                                                          \
+    if (e_ != cudaSuccess) return nfail((n), EP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+static bool shape_ok(const ep_net *n, const int size[3]) {
+  const int m = 1 << (n->u.levels - 1);
+  for (int d = 0; d < n->u.D; ++d)
+    if (size[d] < m || size[d] % m) return false;
+  return true;
+}
+
+extern "C" {
+
+ep_status ep_net_create(int ndim, int in_ch, int out_ch, int base, int levels, unsigned long long seed, void *stream,
+                        ep_net **out) {
+  if (!out || (ndim != 2 && ndim != 3) || in_ch < 1 || out_ch < 1 || base < 1 || levels < 1 || levels > 6)
+    return nfail(nullptr, EP_ERR_ARG, "ep_net_create: bad arguments");
+  ep_net *n = new ep_net();
+  UNet &u = n->u;
+  u.D = ndim; u.cin = in_ch; u.cout = out_ch; u.base = base; u.levels = levels;
+  u.st = (cudaStream_t)stream;
+  unet_layers(u);
+  // He-uniform initialisation from splitmix64 (seeded); biases and the head zero
+  std::vector<float> w(u.nparam, 0.f);
+  unsigned long long st = seed;
+  auto rnd = [&]() {
+    st += 0x9E3779B97F4A7C15ull;
+    unsigned long long z = st;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+  };
+  for (size_t li = 0; li + 1 < u.layers.size(); ++li) {
+    const Layer &L = u.layers[li];
+    long long taps = (long long)L.k * L.k * (ndim == 3 ? L.k : 1);
+    double bound = sqrt(6.0 / (double)(L.cin * taps));
+    for (long long q = 0; q < (long long)L.cin * L.cout * taps; ++q) w[L.woff + q] = (float)((2.0 * rnd() - 1.0) * bound);
+  }
+  const long long np = u.nparam;
+  if (cudaMalloc((void **)&u.w, np * 4) != cudaSuccess || cudaMalloc((void **)&u.g, np * 4) != cudaSuccess ||
+      cudaMalloc((void **)&u.m, np * 4) != cudaSuccess || cudaMalloc((void **)&u.v, np * 4) != cudaSuccess ||
+      cudaMalloc((void **)&u.wb, np * 2) != cudaSuccess || cudaMalloc((void **)&u.dloss, 8) != cudaSuccess) {
+    ep_net_destroy(n);
+    return nfail(nullptr, EP_ERR_OOM, "ep_net_create: allocation failed");
+  }
+  cudaMemcpy(u.w, w.data(), np * 4, cudaMemcpyHostToDevice);
+  cudaMemset(u.m, 0, np * 4);
+  cudaMemset(u.v, 0, np * 4);
+  k_to_bf16<<<nblk(np), NT, 0, u.st>>>(u.w, u.wb, np);
+  if (cudaStreamSynchronize(u.st) != cudaSuccess) {
+    ep_net_destroy(n);
+    return nfail(nullptr, EP_ERR_CUDA, "ep_net_create: initialisation failed");
+  }
+  *out = n;
+  return EP_OK;
+}
+
+ep_status ep_net_param_count(ep_net *n, long long *count) {
+  if (!n || !count) return nfail(n, EP_ERR_ARG, "null argument");
+  *count = n->u.nparam;
+  return EP_OK;
+}
+
+ep_status ep_net_get_params(ep_net *n, float *host, long long count) {
+  if (!n || !host || count != n->u.nparam) return nfail(n, EP_ERR_ARG, "ep_net_get_params: bad arguments");
+  NCK(n, cudaMemcpy(host, n->u.w, count * 4, cudaMemcpyDeviceToHost));
+  return EP_OK;
+}
+
+ep_status ep_net_set_params(ep_net *n, const float *host, long long count) {
+  if (!n || !host || count != n->u.nparam) return nfail(n, EP_ERR_ARG, "ep_net_set_params: bad arguments");
+  NCK(n, cudaMemcpy(n->u.w, host, count * 4, cudaMemcpyHostToDevice));
+  k_to_bf16<<<nblk(count), NT, 0, n->u.st>>>(n->u.w, n->u.wb, count);
+  NCK(n, cudaStreamSynchronize(n->u.st));
+  return EP_OK;
+}
+
+ep_status ep_net_forward(ep_net *n, const float *x, int N, const int size[3], float *y) {
+  if (!n || !x || !y || N < 1 || !size || !shape_ok(n, size))
+    return nfail(n, EP_ERR_ARG, "ep_net_forward: sizes must be multiples of 2^(levels-1)");
+  UNet &u = n->u;
+  NCK(n, ensure_shape(u, N, size[0], size[1], u.D == 3 ? size[2] : 1));
+  if (u.D == 2) forward<2>(u, x); else forward<3>(u, x);
+  const long long no = (long long)N * u.cout * vox(u, 0);
+  NCK(n, cudaMemcpyAsync(y, u.act[indices(u).out], no * 4, cudaMemcpyDeviceToDevice, u.st));
+  NCK(n, cudaGetLastError());
+  return EP_OK;
+}
+
+static ep_status net_grads(ep_net *n, const float *x, const float *t, int N, const int size[3], double *loss) {
+  UNet &u = n->u;
+  NCK(n, ensure_shape(u, N, size[0], size[1], u.D == 3 ? size[2] : 1));
+  if (u.D == 2) forward<2>(u, x); else forward<3>(u, x);
+  const Idx I = indices(u);
+  const long long no = (long long)N * u.cout * vox(u, 0);
+  NCK(n, cudaMemsetAsync(u.dloss, 0, 8, u.st));
+  NCK(n, cudaMemsetAsync(u.g, 0, u.nparam * 4, u.st));
+  k_mse<<<nblk(no), NT, 0, u.st>>>(u.act[I.out], t, u.grad[I.out], no, u.dloss);
+  if (u.D == 2) backward<2>(u, x); else backward<3>(u, x);
+  NCK(n, cudaGetLastError());
+  if (loss) NCK(n, cudaMemcpyAsync(loss, u.dloss, 8, cudaMemcpyDeviceToHost, u.st));
+  NCK(n, cudaStreamSynchronize(u.st));
+  return EP_OK;
+}
+
+ep_status ep_net_gradients(ep_net *n, const float *x, const float *t, int N, const int size[3], double *loss,
+                           float *grad_host, long long count) {
+  if (!n || !x || !t || N < 1 || !size || !shape_ok(n, size) || (grad_host && count != n->u.nparam))
+    return nfail(n, EP_ERR_ARG, "ep_net_gradients: bad arguments");
+  ep_status r = net_grads(n, x, t, N, size, loss);
+  if (r != EP_OK) return r;
+  if (grad_host) NCK(n, cudaMemcpy(grad_host, n->u.g, count * 4, cudaMemcpyDeviceToHost));
+  return EP_OK;
+}
+
+ep_status ep_net_train_step(ep_net *n, const float *x, const float *t, int N, const int size[3], float lr,
+                            double *loss) {
+  if (!n || !x || !t || N < 1 || !size || !shape_ok(n, size) || !(lr > 0.f))
+    return nfail(n, EP_ERR_ARG, "ep_net_train_step: bad arguments");
+  ep_status r = net_grads(n, x, t, N, size, loss);
+  if (r != EP_OK) return r;
+  UNet &u = n->u;
+  u.step += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - powf(b1, (float)u.step), c2 = 1.f - powf(b2, (float)u.step);
+  k_adam<<<nblk(u.nparam), NT, 0, u.st>>>(u.w, u.wb, u.g, u.m, u.v, u.nparam, lr, b1, b2, 1e-8f, c1, c2);
+  NCK(n, cudaGetLastError());
+  NCK(n, cudaStreamSynchronize(u.st));
+  return EP_OK;
+}
+
+ep_status ep_net_destroy(ep_net *n) {
+  if (!n) return EP_OK;
+  UNet &u = n->u;
+  if (u.st) cudaStreamSynchronize(u.st);
+  for (float *p : u.act) cudaFree(p);
+  for (float *p : u.grad) cudaFree(p);
+  cudaFree(u.scratch); cudaFree(u.scratch2);
+  cudaFree(u.w); cudaFree(u.g); cudaFree(u.m); cudaFree(u.v); cudaFree(u.wb); cudaFree(u.dloss);
+  delete n;
+  return EP_OK;
+}
+
+const char *ep_net_last_error(ep_net *n) { return n ? n->err.c_str() : g_net_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,75 @@
+"""Learned warm start: data from the solver's own trajectories, training on
+the GPU with the library's network kernels, and use in later solves.
+
+Each sample is one increment n >= 3 of a plain-start solve.  The features
+(computed by the library before the increment) are the previous increment's
+velocity change at cell centres over its L-infinity norm S, 1 - s and
+c / max(c).  The target (computed after the solve) is this increment's
+velocity change over S minus the previous one.  So the network learns a
+correction to "repeat the last increment", and a zero network reproduces
+that extrapolation.  PyTorch only supplies the device buffers the library
+writes into; every arithmetic step runs in the library.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from ._native import LOAD_XY, LOAD_XZ, Net
+
+
+def new_net(ndim, base=32, levels=3, seed=0, stream=None):
+    """A warm-start network for ndim-dimensional grids (ndim + 2 inputs)."""
+    return Net(ndim, ndim + 2, ndim, base=base, levels=levels, seed=seed, stream=stream)
+
+
+class Samples:
+    """Features and targets of one padded grid size, in device buffers."""
+
+    def __init__(self, ndim, dims, capacity, device="cuda"):
+        import torch
+        self.ndim, self.dims = ndim, tuple(dims)
+        nv = int(np.prod([d for d in dims[:ndim]]))
+        self.nv = nv
+        self.x = torch.zeros((capacity, ndim + 2, nv), dtype=torch.float32, device=device)
+        self.t = torch.zeros((capacity, ndim, nv), dtype=torch.float32, device=device)
+        self.n = 0
+
+    def ptr_x(self, i):
+        return self.x.data_ptr() + i * (self.ndim + 2) * self.nv * 4
+
+    def ptr_t(self, i):
+        return self.t.data_ptr() + i * self.ndim * self.nv * 4
+
+
+def collect(grid, a, dt, increments, samples, load_plane=LOAD_XY, warm=False):
+    """Solve `increments` increments on `grid` (plain start, or the attached
+    network when warm) and store one sample per increment from the third on.
+    Returns the iteration count of each increment."""
+    iters = []
+    for inc in range(1, increments + 1):
+        have = inc >= 3 and samples is not None and samples.n < samples.x.shape[0]
+        scale = None
+        if have:
+            scale = grid.warm_features(samples.ptr_x(samples.n))
+        grid.apply_increment(a, dt, load_plane, use_warm_start=bool(warm and inc >= 3))
+        info = grid.solve_increment()
+        iters.append(info["iters"])
+        if have:
+            grid.warm_target(samples.ptr_x(samples.n), scale, samples.ptr_t(samples.n))
+            samples.n += 1
+    return iters
+
+
+def train(net, groups, steps=400, lr=1e-3, batch=8, seed=0):
+    """Adam on the MSE loss over minibatches of consecutive samples of one
+    padded size (drawn at random); returns the loss history."""
+    rng = np.random.default_rng(seed)
+    losses = []
+    groups = [g for g in groups if g.n > 0]
+    for _ in range(steps):
+        g = groups[rng.integers(len(groups))]
+        nb = min(batch, g.n)
+        i0 = int(rng.integers(0, g.n - nb + 1))
+        size = list(g.dims[:g.ndim])
+        losses.append(net.train_step(g.ptr_x(i0), g.ptr_t(i0), nb, size, lr))
+    return losses

@@ -188,17 +188,38 @@ def test_fp64_body_force_manufactured(P):
     del sp
 
 
+def run_fp32_vs_oracle(P, s, increments, gpu_tol=1e-6, oracle_tol=1e-10):
+    """FP32 mixed GPU solve at its tolerance against a tightly converged FP64
+    oracle: the worst L-infinity-normalised error of each field."""
+    g = gpu_grid(P, s, P.FP32_MIXED, tol=gpu_tol, max_iter=400000)
+    o = O.from_setup(s, tol=oracle_tol)
+    fields = FIELDS_2D if s.ndim == 2 else FIELDS_3D
+    worst = {}
+    for inc in range(1, increments + 1):
+        g.apply_increment_rates(rates_of(s), s.dt)
+        g.solve_increment()
+        o.apply_increment(rates_of(s), s.dt)
+        o.solve_increment()
+        sc = group_scales(o, fields)
+        for f in fields:
+            worst[f] = max(worst.get(f, 0.0), rel_err(g.get(f), o.get(f), sc[f]))
+    g.close()
+    return worst
+
+
 def test_fp32_mixed_within_stated_bounds_2d(P):
-    s = E.config(1, n=(48, 40), tol=1e-8)
-    worst = run_pair(P, s, 8, precision=P.FP32_MIXED, tol_fields=None, same_iters=False, max_iter=200000)
+    """FP32 sweeps with FP64 norms and history: stress within 1e-5 and plastic
+    strain within 1e-4 of the FP64 oracle (L-infinity normalised)."""
+    s = E.config(1, n=(48, 40))
+    worst = run_fp32_vs_oracle(P, s, 8)
     for f in ("txx", "tyy", "txy", "p"):
         assert worst[f] <= 1e-5, (f, worst[f])
     assert worst["epl"] <= 1e-4, worst["epl"]
 
 
 def test_fp32_mixed_within_stated_bounds_3d(P):
-    s = E.config(3, n=(16, 15, 14), tol=1e-8, inclusion_radius=0.15)
-    worst = run_pair(P, s, 7, precision=P.FP32_MIXED, tol_fields=None, same_iters=False, max_iter=200000)
+    s = E.config(3, n=(16, 15, 14), inclusion_radius=0.15)
+    worst = run_fp32_vs_oracle(P, s, 7)
     for f in ("txx", "tyy", "tzz", "txy", "txz", "tyz", "p"):
         assert worst[f] <= 1e-5, (f, worst[f])
     assert worst["epl"] <= 1e-4, worst["epl"]
@@ -271,3 +292,141 @@ def test_torch_workspace_and_stream(P):
     assert rel_err(g.get("p"), o.get("p"), np.abs(o.get("txx")).max()) <= 1e-10
     g.close()
     del ws
+
+
+def run_pair_kernel(P, s, increments, variant, kz, precision=None, tol_fields=1e-10, **solver):
+    precision = P.FP64 if precision is None else precision
+    g = gpu_grid(P, s, precision, **solver)
+    g.set_kernel(variant, kz)
+    o = O.from_setup(s, **solver)
+    fields = FIELDS_3D
+    for inc in range(1, increments + 1):
+        g.apply_increment_rates(rates_of(s), s.dt)
+        ig = g.solve_increment()
+        o.apply_increment(rates_of(s), s.dt)
+        io = o.solve_increment()
+        assert ig["iters"] == io["iters"], (inc, ig["iters"], io["iters"])
+        sc = group_scales(o, fields)
+        for f in fields:
+            e = rel_err(g.get(f), o.get(f), sc[f])
+            assert e <= tol_fields, (inc, f, e)
+    g.close()
+
+
+@pytest.mark.parametrize("n,kz", [((17, 13, 11), 4), ((40, 21, 24), 5), ((33, 9, 7), 64)])
+def test_fused_kernel_fp64_parity_3d(P, n, kz):
+    """The fused one-kernel sweep, instantiated in FP64, against the oracle at
+    1e-10: several x tiles, ragged y tiles and z-chunk boundaries."""
+    s = E.config(3, n=n, tol=1e-9, precision="fp64", inclusion_radius=0.15)
+    run_pair_kernel(P, s, 7, P.KERNEL_FUSED, kz)
+
+
+def test_fused_kernel_fp64_parity_3d_xy_plane(P):
+    s = E.config(3, n=(20, 18, 13), tol=1e-9, precision="fp64", load_plane="xy", inclusion_radius=0.2)
+    run_pair_kernel(P, s, 7, P.KERNEL_FUSED, 6)
+
+
+def test_fused_fp32_matches_staged_fp32(P):
+    """FP32 fused and FP32 staged sweeps agree to FP32 rounding over a fixed
+    number of iterations of a plastic increment."""
+    s = E.config(3, n=(36, 30, 28), tol=1e-6, inclusion_radius=0.15)
+    out = []
+    for variant in (P.KERNEL_STAGED, P.KERNEL_FUSED):
+        g = gpu_grid(P, s, P.FP32_MIXED)
+        g.set_kernel(variant, 8)
+        for inc in range(1, 6):
+            if inc == 5:
+                g.set_solver(tol=0.0, max_iter=400, n_chk=100)
+            g.apply_increment(1.0, s.dt, P.LOAD_XZ)
+            info = g.solve_increment(raise_on_fail=False)
+            if info["status"] != 0:
+                g.commit_increment()
+        out.append({f: g.get(f) for f in FIELDS_3D})
+        g.close()
+    for names in GROUPS.values():
+        present = [f for f in names if f in FIELDS_3D]
+        scale = max(max(np.abs(out[0][f]).max() for f in present), 1e-30)
+        for f in present:
+            assert np.abs(out[1][f] - out[0][f]).max() / scale <= 2e-5, f
+
+
+@pytest.mark.parametrize("tile", [0, 1, 2])
+def test_fused2d_fp64_parity(P, tile):
+    """The fused 2D kernel (a batch of one), in FP64, against the oracle."""
+    s = E.config(1, n=(70, 37), tol=1e-10)
+    g = gpu_grid(P, s, P.FP64)
+    g.set_kernel(P.KERNEL_FUSED, tile)
+    o = O.from_setup(s)
+    for inc in range(1, 8):
+        g.apply_increment(1.0, s.dt, P.LOAD_XY)
+        o.apply_increment([1.0, -1.0], s.dt)
+        ig, io = g.solve_increment(), o.solve_increment()
+        assert ig["iters"] == io["iters"], inc
+        sc = group_scales(o, FIELDS_2D)
+        for f in FIELDS_2D:
+            assert rel_err(g.get(f), o.get(f), sc[f]) <= 1e-10, (inc, f)
+
+
+def _batch_setups():
+    sizes = [(24, 24), (31, 17), (40, 40), (16, 33), (9, 50)]
+    out = []
+    for q, n in enumerate(sizes):
+        out.append(E.Setup("b%d" % q, 2, n, phi_deg=22.0 + 3 * q, c0=1.2e-3 + 1e-4 * q, inclusion_radius=0.1,
+                           inclusion_centre=(0.05 * q - 0.1, 0.02 * q, 0.0), seed=4000 + q, tol=1e-9))
+    return out
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batch_matches_solo_bit_for_bit(P, prec):
+    """Every grid advanced inside a batch equals its own solo solve exactly
+    (same kernel arithmetic, same iteration count), for uneven sizes and
+    materials; FP64 instances also match the oracle."""
+    pr = P.FP64 if prec == "fp64" else P.FP32_MIXED
+    setups = _batch_setups()
+    tol = 1e-9 if prec == "fp64" else 1e-6
+    grids = []
+    for s in setups:
+        g = gpu_grid(P, s, pr, tol=tol, max_iter=400000)
+        g.set_kernel(P.KERNEL_FUSED, 0)
+        grids.append(g)
+    batch = P.Batch(grids)
+    solos = []
+    for s in setups:
+        g = gpu_grid(P, s, pr, tol=tol, max_iter=400000)
+        g.set_kernel(P.KERNEL_FUSED, 0)
+        solos.append(g)
+    oracles = [O.from_setup(s, tol=tol) for s in setups] if prec == "fp64" else None
+    for inc in range(1, 7):
+        batch.apply_increment(1.0, 1e-4)
+        infos, st = batch.solve_increment()
+        for q, (s, g) in enumerate(zip(setups, solos)):
+            g.apply_increment(1.0, 1e-4, P.LOAD_XY)
+            i1 = g.solve_increment()
+            assert infos[q]["iters"] == i1["iters"], (inc, q)
+            for f in FIELDS_2D:
+                assert np.array_equal(grids[q].get(f), g.get(f)), (inc, q, f)
+            if oracles:
+                o = oracles[q]
+                o.apply_increment([1.0, -1.0], 1e-4)
+                io = o.solve_increment()
+                assert io["iters"] == i1["iters"], (inc, q)
+                sc = group_scales(o, FIELDS_2D)
+                for f in FIELDS_2D:
+                    assert rel_err(g.get(f), o.get(f), sc[f]) <= 1e-10, (inc, q, f)
+    batch.close()
+
+
+def test_batch_autotune_picks_a_tile_and_keeps_results(P):
+    setups = _batch_setups()
+    grids = [gpu_grid(P, s, P.FP32_MIXED, tol=1e-6) for s in setups]
+    for g in grids:
+        g.set_kernel(P.KERNEL_FUSED, 0)
+    batch = P.Batch(grids)
+    for inc in range(1, 6):
+        batch.apply_increment(1.0, 1e-4)
+        if inc == 5:
+            tile = batch.autotune(5)
+            assert tile in (0, 1, 2)
+        infos, st = batch.solve_increment()
+        assert st == 0
+    batch.close()
