@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-size", type=int, default=24)
     ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--kernel", default="auto", choices=sorted(["auto", "staged", "fused", "tma"]),
+                    help="sweep kernel: auto (library default), staged, fused (cp.async) or tma")
     return ap.parse_args()
 
 
@@ -190,18 +192,30 @@ def reference_arm(args):
 
 
 # --------------------------------------------------------------- our arm ----
-def make_grid(P, s, precision):
+KERNEL = {"auto": -1, "staged": 0, "fused": 1, "tma": 2}
+
+
+def one_step(P, g, s):
+    """One pass of the path: back to the checkpoint before the timed
+    increment, start it, iterate to tolerance, commit."""
+    g.restore()
+    g.apply_increment(s.a, s.dt, P.LOAD_XZ)
+    return g.solve_increment()
+
+
+def make_grid(P, s, precision, kernel="auto"):
     g = P.Grid(3, s.n, s.L, precision=P.FP64 if precision == "fp64" else P.FP32_MIXED)
+    g.set_kernel(KERNEL[kernel], -1)
     g.set_material(s.K, s.G, s.mu_s, s.phi_deg, s.psi_deg, s.cohesion())
     g.set_solver(tol=s.tol, max_iter=2000000, n_chk=100)
     return g
 
 
-def prepare(P, s, precision, increment, warmup):
+def prepare(P, s, precision, increment, warmup, kernel="auto"):
     """Solve the increments before the timed one; the last `warmup` of them
     are the warm-up steps (full passes of the path: start state, graph
     chunks, commit).  Then checkpoint the history on the device."""
-    g = make_grid(P, s, precision)
+    g = make_grid(P, s, precision, kernel)
     n_before = increment - 1
     for inc in range(1, n_before + 1):
         g.apply_increment(s.a, s.dt, P.LOAD_XZ)
@@ -231,7 +245,7 @@ def our_arm(args):
 
     s = setup_for(args.size, args.tol)
     cells = s.n[0] * s.n[1] * s.n[2]
-    g = prepare(P, s, args.precision, args.increment, args.warmup)
+    g = prepare(P, s, args.precision, args.increment, args.warmup, args.kernel)
     bpc = g.sweep_bytes_per_cell()
     clk = Clocks(local)
     barrier()
@@ -260,7 +274,10 @@ def our_arm(args):
 
     # kernel timing (CUDA events on the library's stream) for the roofline
     ktimes = g.time_sweep(10)
-    kernels = ["strain", "trial", "return_centres", "return_edges", "velocity"]
+    if len(ktimes) == 2:
+        kernels = ["fused_sweep_tma" if args.kernel == "tma" else "fused_sweep"]
+    else:
+        kernels = ["strain", "trial", "return_centres", "return_edges", "velocity"]
     it_ms = ktimes[-1]
     dom = int(max(range(len(kernels)), key=lambda q: ktimes[q]))
 
@@ -321,14 +338,17 @@ def our_arm(args):
         "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
         "config": {"workload": "3d-ep-xz-inclusion %d^3, increment %d, tol %g, %s sweeps, plain start"
                    % (s.n[0], args.increment, args.tol, args.precision),
+                   "sweep_kernel": kernels[0] if len(kernels) == 1 else "staged",
                    "cells": cells, "iterations_per_step": infos[-1]["iters"],
                    "l2": "inputs larger than L2 (every field %.2f GB)" % (cells * 4 / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},
         "ms_per_increment": ms_per_step,
         "clocks": clocks,
-        # per step: (iters / n_chk + 1) graph chunks of 5 n_chk + 1 kernels, plus
-        # about 20 start-of-increment and 7 commit kernels
-        "gpu_launches": int(sum((i["iters"] // 100 + 1) * 501 + 27 for i in infos)),
+        # per step: (iters / n_chk + 1) graph chunks (staged: 5 n_chk + 1
+        # kernels; fused: one staged check iteration, the check and n_chk - 1
+        # fused sweeps), plus about 20 start-of-increment and 7 commit kernels
+        "gpu_launches": int(sum((i["iters"] // 100 + 1) * (501 if len(kernels) == 5 else 105) + 27
+                                for i in infos)),
         "roofline": roof,
         "e2e": e2e,
         "fp64_plain": fp64,

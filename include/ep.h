@@ -154,14 +154,19 @@ ep_status ep_field_count(ep_handle h, int field, size_t *count);
 ep_status ep_get_fields(ep_handle h, int field, double *host_out, size_t count);
 ep_status ep_set_fields(ep_handle h, int field, const double *host_in, size_t count);
 
-/* Sweep kernel selection.  EP_KERNEL_AUTO (default): the fused one-kernel
- * sweep for FP32 grids, the staged five-kernel sweep for FP64 ones (FP64 is
- * bound by FP64 arithmetic on GB300, where the staged sweep does no halo
- * recomputation).  EP_KERNEL_STAGED / EP_KERNEL_FUSED force one; a body force
- * always uses the staged sweep.  shape (< 0 keeps the current): in 3D the
- * z-planes per block of the fused kernel (>= 1); in 2D the tile of the fused
- * kernel (0: 32x8, 1: 32x16, 2: 64x8 cells). */
-enum { EP_KERNEL_AUTO = -1, EP_KERNEL_STAGED = 0, EP_KERNEL_FUSED = 1 };
+/* Sweep kernel selection.  EP_KERNEL_AUTO (default): the fastest measured
+ * kernel for the grid -- the fused one-kernel sweep for FP32 2D grids, the
+ * staged five-kernel sweep otherwise (FP64 is bound by FP64 arithmetic on
+ * GB300, where the staged sweep does no halo recomputation).
+ * EP_KERNEL_STAGED / EP_KERNEL_FUSED force one;
+ * EP_KERNEL_FUSED_TMA is the 3D fused sweep with every plane streamed by
+ * the tensor-memory accelerator (a timed-out copy ends the solve with
+ * EP_ERR_TIMEOUT).  A body force always uses the staged sweep.
+ * shape (< 0 keeps the current): in 3D the z-planes per block of the fused
+ * kernels (0, the default: chosen from the grid size so that the launch
+ * fills every SM); in 2D the tile of the fused kernel (0: 32x8, 1: 32x16,
+ * 2: 64x8 cells). */
+enum { EP_KERNEL_AUTO = -1, EP_KERNEL_STAGED = 0, EP_KERNEL_FUSED = 1, EP_KERNEL_FUSED_TMA = 2 };
 ep_status ep_set_kernel(ep_handle h, int variant, int shape);
 
 /* Batched 2D solves: many grids of any sizes and materials advance through

@@ -20,7 +20,7 @@ STATUS_NAMES = {0: "EP_OK", 1: "EP_ERR_ARG", 2: "EP_ERR_CUDA", 3: "EP_ERR_OOM", 
                 5: "EP_ERR_NOT_CONVERGED", 6: "EP_ERR_DIVERGED", 7: "EP_ERR_TIMEOUT"}
 FP64, FP32_MIXED = 0, 1
 LOAD_XY, LOAD_XZ = 0, 1
-KERNEL_AUTO, KERNEL_STAGED, KERNEL_FUSED = -1, 0, 1
+KERNEL_AUTO, KERNEL_STAGED, KERNEL_FUSED, KERNEL_FUSED_TMA = -1, 0, 1, 2
 
 FIELDS = ["vx", "vy", "vz", "txx", "tyy", "tzz", "txy", "txz", "tyz", "p", "epl",
           "ux", "uy", "uz", "exx", "eyy", "ezz", "exy", "exz", "eyz", "coh", "eii", "scale",

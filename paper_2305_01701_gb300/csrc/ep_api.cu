@@ -56,7 +56,7 @@ struct ep_grid {
   cudaGraphExec_t chunk = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   int variant = EP_KERNEL_AUTO;  // sweep kernel choice (ep_set_kernel)
-  int kz = 64;              // z-planes per CTA of the fused 3D kernel
+  int kz = 0;               // z-planes per CTA of the fused 3D kernel (0: by grid size)
   int tile = 0;             // tile of the fused 2D kernel (0: 32x8, 1: 32x16, 2: 64x8)
   void *inst_dev = nullptr; // this grid as a batch of one (fused 2D)
   int4 *items_dev = nullptr;
@@ -421,11 +421,21 @@ ep_status prologue(ep_grid *h, const double *const dv[3]) {
   return EP_OK;
 }
 
-// The fused kernel serves FP32 3D sweeps without a body force.
+// A fused 3D kernel runs only when asked for (without a body force): on
+// GB300 both fused flavours are slower than the staged sweep (they are bound
+// by shared-memory traffic at one block per SM), so AUTO stays staged.
 template <typename T>
 bool use_fused(const ep_grid *h) {
   if (h->ndim != 3 || h->have_f) return false;
-  return h->variant == EP_KERNEL_FUSED || (h->variant == EP_KERNEL_AUTO && sizeof(T) == 4);
+  return h->variant == EP_KERNEL_FUSED || h->variant == EP_KERNEL_FUSED_TMA;
+}
+
+// one fused 3D iteration in the grid's chosen flavour
+template <typename T>
+bool launch_fused_any(const ep_grid *h, const Stage<T> &S, const DevInfo *di, cudaStream_t st) {
+  if (h->variant == EP_KERNEL_FUSED_TMA) return launch_fused3d_tma<T>(h->g, S, h->dscal, di, h->kz, st);
+  launch_fused3d<T>(h->g, S, h->dscal, di, h->kz, st);
+  return true;
 }
 
 // One chunk of n_chk iterations (first one a check iteration), captured once.
@@ -451,7 +461,12 @@ ep_status capture_chunk(ep_grid *h) {
     Stage<T> S = sweep_stage<T>(h, it & 1);
     const int chk = it == 0;
     if (!chk && use_fused<T>(h)) {
-      launch_fused3d<T>(g, S, h->dscal, h->dinfo, h->kz, h->cap);
+      if (!launch_fused_any<T>(h, S, h->dinfo, h->cap)) {
+        cudaGraph_t gr;
+        cudaStreamEndCapture(h->cap, &gr);
+        if (gr) cudaGraphDestroy(gr);
+        return fail(h, EP_ERR_CUDA, "tensor map encoding failed");
+      }
       continue;
     }
     launch_strain<T>(g, S, h->dscal, h->dinfo, h->cap);
@@ -510,7 +525,8 @@ ep_status solve(ep_grid *h, ep_solve_info *info) {
     if (h->hinfo->done) break;
   }
   const DevInfo di = *h->hinfo;
-  ep_status st = di.done == 1 ? EP_OK : di.done == 2 ? EP_ERR_DIVERGED : EP_ERR_NOT_CONVERGED;
+  ep_status st = di.done == 1 ? EP_OK : di.done == 2 ? EP_ERR_DIVERGED : di.done == 4 ? EP_ERR_TIMEOUT
+                                                                                    : EP_ERR_NOT_CONVERGED;
   unsigned long long npl = 0;
   double line[2] = {0, 0};
   if (st != EP_OK) {
@@ -542,6 +558,7 @@ ep_status solve(ep_grid *h, ep_solve_info *info) {
     info->status = st;
   }
   if (st == EP_ERR_DIVERGED) return fail(h, st, "NaN in a residual norm");
+  if (st == EP_ERR_TIMEOUT) return fail(h, st, "a bounded device wait gave up");
   if (st == EP_ERR_NOT_CONVERGED) return fail(h, st, "max_iter reached before eps_res <= tol");
   return EP_OK;
 }
@@ -629,7 +646,8 @@ ep_status ep_create_grid(int ndim, const int n[3], const double L[3], ep_precisi
     ep_destroy(h);
     return fail(nullptr, EP_ERR_CUDA, "ep_create_grid: stream/event/pinned allocation failed");
   }
-  if (fused3d_configure() != cudaSuccess || fused2d_configure() != cudaSuccess) {
+  if (fused3d_configure() != cudaSuccess || fused2d_configure() != cudaSuccess ||
+      fused3d_tma_configure() != cudaSuccess) {
     ep_destroy(h);
     return fail(nullptr, EP_ERR_CUDA, "ep_create_grid: fused kernel shared-memory attribute");
   }
@@ -997,8 +1015,9 @@ ep_status ep_time_sweep(ep_handle h, int iters, double *ms_out, int n_out, int *
   if (fused) {
     for (int it = 0; it < iters; ++it) {
       CK(h, cudaEventRecord(ev[0], h->stream));
-      if (h->prec == EP_FP64) launch_fused3d<double>(h->g, sweep_stage<double>(h, it & 1), h->dscal, nullptr, h->kz, h->stream);
-      else launch_fused3d<float>(h->g, sweep_stage<float>(h, it & 1), h->dscal, nullptr, h->kz, h->stream);
+      bool ok = h->prec == EP_FP64 ? launch_fused_any<double>(h, sweep_stage<double>(h, it & 1), nullptr, h->stream)
+                                   : launch_fused_any<float>(h, sweep_stage<float>(h, it & 1), nullptr, h->stream);
+      if (!ok) return fail(h, EP_ERR_CUDA, "tensor map encoding failed");
       CK(h, cudaEventRecord(ev[1], h->stream));
       CK(h, cudaGetLastError());
       CK(h, cudaEventSynchronize(ev[1]));
@@ -1051,10 +1070,12 @@ ep_status ep_time_sweep(ep_handle h, int iters, double *ms_out, int n_out, int *
 
 ep_status ep_set_kernel(ep_handle h, int variant, int shape) {
   if (!h) return fail(nullptr, EP_ERR_ARG, "null handle");
-  if (variant < EP_KERNEL_AUTO || variant > EP_KERNEL_FUSED)
+  if (variant < EP_KERNEL_AUTO || variant > EP_KERNEL_FUSED_TMA)
     return fail(h, EP_ERR_ARG, "ep_set_kernel: unknown variant");
-  if (shape >= 0 && ((h->ndim == 3 && shape < 1) || (h->ndim == 2 && shape > 2)))
-    return fail(h, EP_ERR_ARG, "ep_set_kernel: shape is z-planes >= 1 (3D) or a tile 0..2 (2D)");
+  if (variant == EP_KERNEL_FUSED_TMA && h->ndim != 3)
+    return fail(h, EP_ERR_ARG, "ep_set_kernel: the TMA sweep is 3D only");
+  if (shape >= 0 && h->ndim == 2 && shape > 2)
+    return fail(h, EP_ERR_ARG, "ep_set_kernel: shape is z-planes (3D, 0: by grid size) or a tile 0..2 (2D)");
   if (h->chunk) {
     cudaGraphExecDestroy(h->chunk);
     h->chunk = nullptr;

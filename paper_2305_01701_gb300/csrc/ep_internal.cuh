@@ -159,11 +159,31 @@ void launch_velocity(const Geo &g, const Stage<T> &S, const Scal *sc, DevInfo *d
 void launch_check(DevInfo *di, const Scal *sc, cudaStream_t st);
 
 // ---- fused sweeps (ep_fused3d.cu) ------------------------------------
+// z-planes per block when none was chosen (kz <= 0): split z until the grid
+// holds about two blocks per SM, between 8 and 64 planes per block (each
+// block re-reads four halo planes, so deeper blocks move fewer bytes)
+inline int fused3d_kz(const Geo &g, int tx, int ty, int kz) {
+  if (kz > 0) return kz;
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 148;
+  }
+  const long long cols = (long long)((g.px + tx - 1) / tx) * ((g.py + ty - 1) / ty);
+  long long chunks = (2LL * sms + cols - 1) / cols;
+  int k = (int)((g.pz + chunks - 1) / chunks);
+  return k < 8 ? 8 : (k > 64 ? 64 : k);
+}
 template <typename T>
 size_t fused3d_smem_bytes();
 cudaError_t fused3d_configure();
 template <typename T>
 void launch_fused3d(const Geo &g, const Stage<T> &S, const Scal *sc, const DevInfo *di, int kz, cudaStream_t st);
+// TMA-streamed variant (ep_fused3d_tma.cu); false if a tensor map failed
+template <typename T>
+bool launch_fused3d_tma(const Geo &g, const Stage<T> &S, const Scal *sc, const DevInfo *di, int kz, cudaStream_t st);
+cudaError_t fused3d_tma_configure();
 
 // ---- increment set-up and commit (FP64; ep_increment.cu) ------------------
 struct History {
