@@ -1,18 +1,22 @@
 #!/usr/bin/env python3
 """Benchmark of the pseudo-transient elasto-plastic solve on GB300.
 
-Workload (default): the 3D elasto-plastic box of 511^3 cells under x-z pure
+Workload (default): the 3D elasto-plastic box of 127^3 cells under x-z pure
 shear with a spherical weak inclusion (radius 0.05, half cohesion) and +-1%
 seeded cohesion noise; K = 2, G = 1, c = 1.5e-3 G, phi = 30 deg, strain
-increment 1e-4, tolerance 1e-6.  One step is one load increment solved to
-tolerance (start state, pseudo-transient sweeps, FP64 commit): the first
-increment at which the inclusion yields (increment 5), re-solved from a
-device checkpoint each step so that every step does the same work.  The
-warm-up steps are the increments just before it, each a full pass of the
-same path.
+increment 1e-4, tolerance 1e-6; FP32 sweeps with FP64 norms, convergence
+test and history.  One step is one load increment solved to tolerance
+(start state, pseudo-transient sweeps, FP64 commit): the first increment at
+which the inclusion yields (increment 5), re-solved from a device checkpoint
+each step so that every step does the same work.  The same increment is
+then solved once with plain FP64 sweeps ("fp64_plain").
+
+--size 511 runs the 511^3 box of the same setup.  Its first plastic
+increment needs well over 10^4 iterations (hours in FP64), so it is not the
+default step.
 
 Metric: effective HBM throughput of the sweeps (algorithmic bytes per cell
-per iteration x cells x iterations / wall time) and the wall time per
+per iteration x cells x iterations / device time) and the wall time per
 increment.  With --gpus N (torchrun), each rank solves its own replica (the
 solve does not shard: no data-path collective) and value is the sum over
 ranks divided by the slowest rank's time.
@@ -42,16 +46,16 @@ def parse():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--size", type=int, default=511, help="cells per side of the 3D box")
+    ap.add_argument("--size", type=int, default=127, help="cells per side of the 3D box")
     ap.add_argument("--increment", type=int, default=5, help="load increment that is timed")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
-    ap.add_argument("--fp64-compare", action="store_true", help="also time the plain FP64 solve")
+    ap.add_argument("--no-fp64", action="store_true", help="skip timing the plain FP64 solve")
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-size", type=int, default=24)
     ap.add_argument("--e2e-steps", type=int, default=1)
-    ap.add_argument("--kernel", default="auto", choices=sorted(["auto", "staged", "fused", "tma"]),
-                    help="sweep kernel: auto (library default), staged, fused (cp.async) or tma")
+    ap.add_argument("--kernel", default="auto", choices=sorted(["auto", "staged", "fused", "tma", "reg"]),
+                    help="sweep kernel: auto (library default), staged, fused (cp.async), tma or reg")
     return ap.parse_args()
 
 
@@ -192,7 +196,7 @@ def reference_arm(args):
 
 
 # --------------------------------------------------------------- our arm ----
-KERNEL = {"auto": -1, "staged": 0, "fused": 1, "tma": 2}
+KERNEL = {"auto": -1, "staged": 0, "fused": 1, "tma": 2, "reg": 3}
 
 
 def one_step(P, g, s):
@@ -203,28 +207,42 @@ def one_step(P, g, s):
     return g.solve_increment()
 
 
-def make_grid(P, s, precision, kernel="auto"):
-    g = P.Grid(3, s.n, s.L, precision=P.FP64 if precision == "fp64" else P.FP32_MIXED)
+def make_grid(P, s, precision, kernel="auto", stream=None):
+    g = P.Grid(3, s.n, s.L, precision=P.FP64 if precision == "fp64" else P.FP32_MIXED, stream=stream)
     g.set_kernel(KERNEL[kernel], -1)
     g.set_material(s.K, s.G, s.mu_s, s.phi_deg, s.psi_deg, s.cohesion())
     g.set_solver(tol=s.tol, max_iter=2000000, n_chk=100)
     return g
 
 
-def prepare(P, s, precision, increment, warmup, kernel="auto"):
-    """Solve the increments before the timed one; the last `warmup` of them
-    are the warm-up steps (full passes of the path: start state, graph
-    chunks, commit).  Then checkpoint the history on the device."""
-    g = make_grid(P, s, precision, kernel)
-    n_before = increment - 1
-    for inc in range(1, n_before + 1):
+def prepare(P, s, precision, increment, kernel="auto", stream=None):
+    """Solve the increments before the timed one, then checkpoint the
+    history on the device (every step restarts from it)."""
+    g = make_grid(P, s, precision, kernel, stream)
+    for inc in range(1, increment):
         g.apply_increment(s.a, s.dt, P.LOAD_XZ)
         g.solve_increment()
     g.snapshot()
-    extra = max(0, warmup - n_before)      # more warm-up than increments before
-    for _ in range(extra):
-        one_step(P, g, s)
     return g
+
+
+def timed_steps(torch, P, g, s, stream, steps, barrier):
+    """Run `steps` steps between CUDA events on the library's stream (with a
+    barrier and a device synchronisation on both sides); returns (device
+    seconds, solve infos)."""
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0.record(stream)
+    infos = [one_step(P, g, s) for _ in range(steps)]
+    ev1.record(stream)
+    barrier()
+    return ev0.elapsed_time(ev1) * 1e-3, infos
+
+
+def kernel_names(ktimes, kernel):
+    if len(ktimes) == 2:
+        return [{"tma": "k_fused3d_tma", "reg": "k_fused3d_reg", "fused": "k_fused3d"}.get(kernel, "k_fused3d_reg")]
+    return ["k_strain", "k_trial", "k_return_centres", "k_return_edges", "k_velocity"]
 
 
 def our_arm(args):
@@ -243,72 +261,63 @@ def our_arm(args):
         if dist:
             dist.barrier()
 
+    stream = torch.cuda.Stream()
     s = setup_for(args.size, args.tol)
     cells = s.n[0] * s.n[1] * s.n[2]
-    g = prepare(P, s, args.precision, args.increment, args.warmup, args.kernel)
+    g = prepare(P, s, args.precision, args.increment, args.kernel, stream.cuda_stream)
+    for _ in range(args.warmup):           # full passes of the timed step
+        one_step(P, g, s)
     bpc = g.sweep_bytes_per_cell()
     clk = Clocks(local)
-    barrier()
     clk.start()
-    t0 = time.perf_counter()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record()
-    infos = []
-    for _ in range(args.steps):
-        infos.append(one_step(P, g, s))
-    ev1.record()
-    barrier()
-    wall = time.perf_counter() - t0
+    sec, infos = timed_steps(torch, P, g, s, stream, args.steps, barrier)
     clocks = clk.stop()
-    # per-rank time: the host-side wall clock (the solve is synchronous per step)
-    tmax = wall
+    tmax = sec
     if dist:
-        t = torch.tensor([wall], device="cuda", dtype=torch.float64)
+        t = torch.tensor([sec], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         tmax = float(t.item())
     iters = sum(i["iters"] for i in infos)
-    my_bytes = bpc * cells * iters
-    total_bytes = my_bytes * world
-    gbs = total_bytes / tmax / 1e9
+    gbs = bpc * cells * iters * world / tmax / 1e9
     ms_per_step = tmax / args.steps * 1e3
 
-    # kernel timing (CUDA events on the library's stream) for the roofline
-    ktimes = g.time_sweep(10)
-    if len(ktimes) == 2:
-        kernels = ["fused_sweep_tma" if args.kernel == "tma" else "fused_sweep"]
-    else:
-        kernels = ["strain", "trial", "return_centres", "return_edges", "velocity"]
+    # dominant sweep kernel: CUDA events on the library's stream around a
+    # burst of back-to-back launches on the same increment
+    ktimes = g.time_sweep(20)
+    kernels = kernel_names(ktimes, args.kernel)
     it_ms = ktimes[-1]
     dom = int(max(range(len(kernels)), key=lambda q: ktimes[q]))
 
-    # end-to-end through the C ABI with host buffers: scalars in, fields out
+    # end to end through the C ABI with host buffers: the step's inputs (load
+    # rates, time step) in, the converged fields out to pinned host memory
     e2e = None
     if args.e2e_steps > 0:
-        fields = ["vx", "vy", "vz", "epl"]
+        fields = ["vx", "vy", "vz", "txx", "tyy", "tzz", "txy", "txz", "tyz", "p", "epl"]
         bufs = {f: torch.empty(g.count(f), dtype=torch.float64, pin_memory=True) for f in fields}
         d2h = sum(b.numel() * 8 for b in bufs.values())
-        h2d = 8 * 3 + 8  # rates and dt
+        h2d = 8 * 3 + 8
+        barrier()
         t0 = time.perf_counter()
         e_iters = 0
         for _ in range(args.e2e_steps):
-            g.restore()
-            g.apply_increment(s.a, s.dt, P.LOAD_XZ)
-            e_iters += g.solve_increment()["iters"]
+            e_iters += one_step(P, g, s)["iters"]
             for f in fields:
                 g.get_into(f, bufs[f].data_ptr(), bufs[f].numel())
+        barrier()
         et = time.perf_counter() - t0
         e2e = {"value": bpc * cells * e_iters * world / et / 1e9, "unit": "GB/s",
                "ms_per_step": et / args.e2e_steps * 1e3, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     fp64 = None
-    if args.fp64_compare:
+    if not args.no_fp64:
         g.close()
-        g64 = prepare(P, s, "fp64", args.increment, 0)
-        t0 = time.perf_counter()
-        i64 = one_step(P, g64, s)
-        t64 = time.perf_counter() - t0
-        fp64 = {"ms_per_increment": t64 * 1e3, "iterations": i64["iters"],
-                "GB_per_s": g64.sweep_bytes_per_cell() * cells * i64["iters"] / t64 / 1e9}
+        g64 = prepare(P, s, "fp64", args.increment, "auto", stream.cuda_stream)
+        one_step(P, g64, s)
+        t64, i64 = timed_steps(torch, P, g64, s, stream, 1, barrier)
+        i64 = i64[0]
+        fp64 = {"ms_per_increment": t64 * 1e3, "iterations": i64["iters"], "kernel": "staged",
+                "GB_per_s": g64.sweep_bytes_per_cell() * cells * i64["iters"] / t64 / 1e9,
+                "fp32_speedup": t64 * 1e3 / ms_per_step}
         g64.close()
 
     cpu = None
@@ -326,12 +335,11 @@ def our_arm(args):
         pass
     hbm = peaks.get("hbm_gbs", 6800.0)
     achieved = bpc * cells / (it_ms * 1e-3) / 1e9
-    roof = {"bound": "hbm", "kernel": "whole sweep iteration (%d stage kernels, dominant: %s)"
-                                      % (len(kernels), kernels[dom]),
+    roof = {"bound": "hbm", "kernel": kernels[0] if len(kernels) == 1 else "staged sweep (5 kernels)",
             "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-            "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6800 GB/s",
+            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6800 GB/s",
             "traffic": None, "kernel_ms": {k: float(ktimes[q]) for q, k in enumerate(kernels)},
-            "iteration_ms": float(it_ms), "alg_bytes_per_cell": bpc}
+            "dominant": kernels[dom], "iteration_ms": float(it_ms), "alg_bytes_per_cell": bpc}
     line = {
         "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -340,7 +348,7 @@ def our_arm(args):
                    % (s.n[0], args.increment, args.tol, args.precision),
                    "sweep_kernel": kernels[0] if len(kernels) == 1 else "staged",
                    "cells": cells, "iterations_per_step": infos[-1]["iters"],
-                   "l2": "inputs larger than L2 (every field %.2f GB)" % (cells * 4 / 1e9),
+                   "l2": "inputs larger than L2 (%d sweep arrays of %.1f MB)" % (33, cells * 4 / 1e6),
                    "parallelism": "replicas" if world > 1 else "single"},
         "ms_per_increment": ms_per_step,
         "clocks": clocks,

@@ -161,12 +161,13 @@ ep_status ep_set_fields(ep_handle h, int field, const double *host_in, size_t co
  * EP_KERNEL_STAGED / EP_KERNEL_FUSED force one;
  * EP_KERNEL_FUSED_TMA is the 3D fused sweep with every plane streamed by
  * the tensor-memory accelerator (a timed-out copy ends the solve with
- * EP_ERR_TIMEOUT).  A body force always uses the staged sweep.
+ * EP_ERR_TIMEOUT); EP_KERNEL_FUSED_REG is the 3D fused sweep that keeps the
+ * z-march in registers (lanes own x columns, warps own y rows).  A body force always uses the staged sweep.
  * shape (< 0 keeps the current): in 3D the z-planes per block of the fused
  * kernels (0, the default: chosen from the grid size so that the launch
  * fills every SM); in 2D the tile of the fused kernel (0: 32x8, 1: 32x16,
  * 2: 64x8 cells). */
-enum { EP_KERNEL_AUTO = -1, EP_KERNEL_STAGED = 0, EP_KERNEL_FUSED = 1, EP_KERNEL_FUSED_TMA = 2 };
+enum { EP_KERNEL_AUTO = -1, EP_KERNEL_STAGED = 0, EP_KERNEL_FUSED = 1, EP_KERNEL_FUSED_TMA = 2, EP_KERNEL_FUSED_REG = 3 };
 ep_status ep_set_kernel(ep_handle h, int variant, int shape);
 
 /* Batched 2D solves: many grids of any sizes and materials advance through

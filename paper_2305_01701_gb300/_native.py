@@ -20,7 +20,7 @@ STATUS_NAMES = {0: "EP_OK", 1: "EP_ERR_ARG", 2: "EP_ERR_CUDA", 3: "EP_ERR_OOM", 
                 5: "EP_ERR_NOT_CONVERGED", 6: "EP_ERR_DIVERGED", 7: "EP_ERR_TIMEOUT"}
 FP64, FP32_MIXED = 0, 1
 LOAD_XY, LOAD_XZ = 0, 1
-KERNEL_AUTO, KERNEL_STAGED, KERNEL_FUSED, KERNEL_FUSED_TMA = -1, 0, 1, 2
+KERNEL_AUTO, KERNEL_STAGED, KERNEL_FUSED, KERNEL_FUSED_TMA, KERNEL_FUSED_REG = -1, 0, 1, 2, 3
 
 FIELDS = ["vx", "vy", "vz", "txx", "tyy", "tzz", "txy", "txz", "tyz", "p", "epl",
           "ux", "uy", "uz", "exx", "eyy", "ezz", "exy", "exz", "eyz", "coh", "eii", "scale",
@@ -237,7 +237,8 @@ class Grid:
         return out.reshape(field_shape(self.ndim, self.n + (1,), name))
 
     def set_kernel(self, variant=-1, kz=0):
-        """-1 auto, 0 staged (five kernels), 1 fused (one kernel, 3D); kz planes per block."""
+        """-1 auto, 0 staged (five kernels), 1 fused (cp.async), 2 fused (TMA, 3D),
+        3 fused (register z-march, 3D); kz planes per block (0: by grid size)."""
         check(self.h, self._L.ep_set_kernel(self.h, int(variant), int(kz)))
 
     def snapshot(self):

@@ -71,6 +71,7 @@ struct ep_grid {
   unsigned long long *wscale = nullptr;
   char *snap = nullptr;     // checkpoint of the history (ep_snapshot)
   bool snap_started = false;
+  int snap_commits = 0;
   std::string err;
 };
 
@@ -427,13 +428,17 @@ ep_status prologue(ep_grid *h, const double *const dv[3]) {
 template <typename T>
 bool use_fused(const ep_grid *h) {
   if (h->ndim != 3 || h->have_f) return false;
-  return h->variant == EP_KERNEL_FUSED || h->variant == EP_KERNEL_FUSED_TMA;
+  return h->variant == EP_KERNEL_FUSED || h->variant == EP_KERNEL_FUSED_TMA || h->variant == EP_KERNEL_FUSED_REG;
 }
 
 // one fused 3D iteration in the grid's chosen flavour
 template <typename T>
 bool launch_fused_any(const ep_grid *h, const Stage<T> &S, const DevInfo *di, cudaStream_t st) {
   if (h->variant == EP_KERNEL_FUSED_TMA) return launch_fused3d_tma<T>(h->g, S, h->dscal, di, h->kz, st);
+  if (h->variant == EP_KERNEL_FUSED_REG) {
+    launch_fused3d_reg<T>(h->g, S, h->dscal, di, h->kz, st);
+    return true;
+  }
   launch_fused3d<T>(h->g, S, h->dscal, di, h->kz, st);
   return true;
 }
@@ -647,7 +652,7 @@ ep_status ep_create_grid(int ndim, const int n[3], const double L[3], ep_precisi
     return fail(nullptr, EP_ERR_CUDA, "ep_create_grid: stream/event/pinned allocation failed");
   }
   if (fused3d_configure() != cudaSuccess || fused2d_configure() != cudaSuccess ||
-      fused3d_tma_configure() != cudaSuccess) {
+      fused3d_tma_configure() != cudaSuccess || fused3d_reg_configure() != cudaSuccess) {
     ep_destroy(h);
     return fail(nullptr, EP_ERR_CUDA, "ep_create_grid: fused kernel shared-memory attribute");
   }
@@ -944,7 +949,10 @@ ep_status ep_set_fields(ep_handle h, int f, const double *in, size_t count) {
 static std::vector<double *> history_arrays(ep_grid *h) {
   std::vector<double *> v;
   const int nd = h->ndim, ns = n_shear(nd);
-  for (int d = 0; d < nd; ++d) { v.push_back(h->H.v[d]); v.push_back(h->H.tn[d]); v.push_back(h->H.u[d]); v.push_back(h->H.an[d]); }
+  for (int d = 0; d < nd; ++d) {
+    v.push_back(h->H.v[d]); v.push_back(h->H.tn[d]); v.push_back(h->H.u[d]); v.push_back(h->H.an[d]);
+    v.push_back(h->vpp[d]);  // the warm start's previous increment
+  }
   for (int c = 0; c < ns; ++c) { v.push_back(h->H.ts[c]); v.push_back(h->H.as[c]); }
   v.push_back(h->H.p);
   v.push_back(h->H.epl);
@@ -960,6 +968,7 @@ ep_status ep_snapshot(ep_handle h) {
     CK(h, cudaMemcpyAsync(h->snap + q * nb, arr[q], nb, cudaMemcpyDeviceToDevice, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
   h->snap_started = h->started;
+  h->snap_commits = h->n_commits;
   return EP_OK;
 }
 
@@ -972,6 +981,7 @@ ep_status ep_restore(ep_handle h) {
     CK(h, cudaMemcpyAsync(arr[q], h->snap + q * nb, nb, cudaMemcpyDeviceToDevice, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
   h->started = h->snap_started;
+  h->n_commits = h->snap_commits;
   h->in_increment = false;
   return EP_OK;
 }
@@ -1070,10 +1080,10 @@ ep_status ep_time_sweep(ep_handle h, int iters, double *ms_out, int n_out, int *
 
 ep_status ep_set_kernel(ep_handle h, int variant, int shape) {
   if (!h) return fail(nullptr, EP_ERR_ARG, "null handle");
-  if (variant < EP_KERNEL_AUTO || variant > EP_KERNEL_FUSED_TMA)
+  if (variant < EP_KERNEL_AUTO || variant > EP_KERNEL_FUSED_REG)
     return fail(h, EP_ERR_ARG, "ep_set_kernel: unknown variant");
-  if (variant == EP_KERNEL_FUSED_TMA && h->ndim != 3)
-    return fail(h, EP_ERR_ARG, "ep_set_kernel: the TMA sweep is 3D only");
+  if ((variant == EP_KERNEL_FUSED_TMA || variant == EP_KERNEL_FUSED_REG) && h->ndim != 3)
+    return fail(h, EP_ERR_ARG, "ep_set_kernel: the TMA and register sweeps are 3D only");
   if (shape >= 0 && h->ndim == 2 && shape > 2)
     return fail(h, EP_ERR_ARG, "ep_set_kernel: shape is z-planes (3D, 0: by grid size) or a tile 0..2 (2D)");
   if (h->chunk) {

@@ -184,6 +184,10 @@ void launch_fused3d(const Geo &g, const Stage<T> &S, const Scal *sc, const DevIn
 template <typename T>
 bool launch_fused3d_tma(const Geo &g, const Stage<T> &S, const Scal *sc, const DevInfo *di, int kz, cudaStream_t st);
 cudaError_t fused3d_tma_configure();
+// register z-march variant (ep_fused3d_reg.cu)
+template <typename T>
+void launch_fused3d_reg(const Geo &g, const Stage<T> &S, const Scal *sc, const DevInfo *di, int kz, cudaStream_t st);
+cudaError_t fused3d_reg_configure();
 
 // ---- increment set-up and commit (FP64; ep_increment.cu) ------------------
 struct History {

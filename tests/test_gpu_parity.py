@@ -313,7 +313,7 @@ def run_pair_kernel(P, s, increments, variant, kz, precision=None, tol_fields=1e
     g.close()
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 @pytest.mark.parametrize("n,kz", [((17, 13, 11), 4), ((40, 21, 24), 5), ((33, 9, 7), 64), ((70, 20, 30), 0)])
 def test_fused_kernel_fp64_parity_3d(P, n, kz, variant):
     """The fused one-kernel sweeps (cp.async and TMA plane streaming),
@@ -323,7 +323,7 @@ def test_fused_kernel_fp64_parity_3d(P, n, kz, variant):
     run_pair_kernel(P, s, 7, variant, kz)
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 def test_fused_kernel_fp64_parity_3d_xy_plane(P, variant):
     s = E.config(3, n=(20, 18, 13), tol=1e-9, precision="fp64", load_plane="xy", inclusion_radius=0.2)
     run_pair_kernel(P, s, 7, variant, 6)
@@ -334,7 +334,7 @@ def test_fused_fp32_matches_staged_fp32(P):
     number of iterations of a plastic increment."""
     s = E.config(3, n=(36, 30, 28), tol=1e-6, inclusion_radius=0.15)
     out = []
-    for variant in (P.KERNEL_STAGED, P.KERNEL_FUSED, P.KERNEL_FUSED_TMA):
+    for variant in (P.KERNEL_STAGED, P.KERNEL_FUSED, P.KERNEL_FUSED_TMA, P.KERNEL_FUSED_REG):
         g = gpu_grid(P, s, P.FP32_MIXED)
         g.set_kernel(variant, 8)
         for inc in range(1, 6):
@@ -350,7 +350,7 @@ def test_fused_fp32_matches_staged_fp32(P):
         present = [f for f in names if f in FIELDS_3D]
         scale = max(max(np.abs(out[0][f]).max() for f in present), 1e-30)
         for f in present:
-            for k in (1, 2):
+            for k in (1, 2, 3):
                 assert np.abs(out[k][f] - out[0][f]).max() / scale <= 2e-5, (k, f)
 
 
