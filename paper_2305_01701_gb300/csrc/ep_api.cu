@@ -1084,6 +1084,8 @@ ep_status ep_set_kernel(ep_handle h, int variant, int shape) {
     return fail(h, EP_ERR_ARG, "ep_set_kernel: unknown variant");
   if ((variant == EP_KERNEL_FUSED_TMA || variant == EP_KERNEL_FUSED_REG) && h->ndim != 3)
     return fail(h, EP_ERR_ARG, "ep_set_kernel: the TMA and register sweeps are 3D only");
+  if (variant == EP_KERNEL_FUSED_REG && h->g.box >= (1LL << 31))
+    return fail(h, EP_ERR_ARG, "ep_set_kernel: the register sweep indexes with 32 bits (box below 2^31 elements)");
   if (shape >= 0 && h->ndim == 2 && shape > 2)
     return fail(h, EP_ERR_ARG, "ep_set_kernel: shape is z-planes (3D, 0: by grid size) or a tile 0..2 (2D)");
   if (h->chunk) {

@@ -339,7 +339,7 @@ void launch_fused3d(const Geo &g, const Stage<T> &S, const Scal *sc, const DevIn
     A.tbn[d] = S.tbn[d]; A.tbs[d] = S.tbs[d]; A.rq[d] = S.rq[d]; A.uo[d] = S.uo[d];
   }
   A.sop = S.sop; A.snp = S.snp; A.pb = S.pb; A.yc = S.yc; A.rd[0] = S.rd[0]; A.rd[1] = S.rd[1];
-  kz = fused3d_kz(g, TX, TY, kz);
+  kz = fused3d_kz(g, TX, TY, kz, 2);
   dim3 grid((g.px + TX - 1) / TX, (g.py + TY - 1) / TY, (g.pz + kz - 1) / kz);
   k_fused3d<T, TY><<<grid, TX * TY, sizeof(Smem<T, TY>), st>>>(g, A, sc, di, kz);
 }

@@ -159,10 +159,11 @@ void launch_velocity(const Geo &g, const Stage<T> &S, const Scal *sc, DevInfo *d
 void launch_check(DevInfo *di, const Scal *sc, cudaStream_t st);
 
 // ---- fused sweeps (ep_fused3d.cu) ------------------------------------
-// z-planes per block when none was chosen (kz <= 0): split z until the grid
-// holds about two blocks per SM, between 8 and 64 planes per block (each
-// block re-reads four halo planes, so deeper blocks move fewer bytes)
-inline int fused3d_kz(const Geo &g, int tx, int ty, int kz) {
+// z-planes per block when none was chosen (kz <= 0).  A block marches kz
+// planes plus four halo planes, and the launch runs in waves of
+// (SMs x blocks per SM) blocks, so the time goes as
+// waves(kz) x (kz + 4); take the kz in [8, 128] that minimises it.
+inline int fused3d_kz(const Geo &g, int tx, int ty, int kz, int per_sm = 1) {
   if (kz > 0) return kz;
   static int sms = 0;
   if (sms == 0) {
@@ -171,9 +172,15 @@ inline int fused3d_kz(const Geo &g, int tx, int ty, int kz) {
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 148;
   }
   const long long cols = (long long)((g.px + tx - 1) / tx) * ((g.py + ty - 1) / ty);
-  long long chunks = (2LL * sms + cols - 1) / cols;
-  int k = (int)((g.pz + chunks - 1) / chunks);
-  return k < 8 ? 8 : (k > 64 ? 64 : k);
+  const long long wave = (long long)sms * per_sm;
+  int best = 8;
+  long long best_cost = -1;
+  for (int k = 8; k <= 128; ++k) {
+    const long long blocks = cols * ((g.pz + k - 1) / k);
+    const long long cost = (blocks + wave - 1) / wave * (k + 4);
+    if (best_cost < 0 || cost < best_cost) { best_cost = cost; best = k; }
+  }
+  return best;
 }
 template <typename T>
 size_t fused3d_smem_bytes();
