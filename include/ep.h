@@ -209,6 +209,21 @@ ep_status ep_net_get_params(ep_net_handle n, float *host, long long count);
 ep_status ep_net_set_params(ep_net_handle n, const float *host, long long count);
 /* y (device, N x out_ch x ...) = net(x); size = {X, Y[, Z]} */
 ep_status ep_net_forward(ep_net_handle n, const float *x, int N, const int size[3], float *y);
+/* ep_net_forward without any allocation.  The paper has no counterpart: this
+ * serves callers that must not allocate device memory while they run -- a
+ * solver loop applying the warm start between increments on a device whose
+ * memory its arena and the caller's allocator pool already hold (a new
+ * cudaMalloc may fail there), and latency-bound loops (cudaMalloc/cudaFree
+ * synchronise the whole device).  The activations live in one static device
+ * array of EP_NET_STATIC_FLOATS floats (64 MiB) inside the library, shared by
+ * every call on a device: shapes whose activations need more return
+ * EP_ERR_ARG (use ep_net_forward), and calls whose kernels may overlap on the
+ * GPU (different streams with no ordering between them) race on it.  Nothing
+ * in it has to start at zero.  The first call on a device looks up the
+ * array's address with that device current; make it before any stream
+ * capture.  Arguments, layout and stream are those of ep_net_forward. */
+#define EP_NET_STATIC_FLOATS (16LL * 1024 * 1024)
+ep_status ep_net_forward_static(ep_net_handle n, const float *x, int N, const int size[3], float *y);
 /* MSE loss mean((net(x) - t)^2) and its parameter gradient (host, nullable) */
 ep_status ep_net_gradients(ep_net_handle n, const float *x, const float *t, int N, const int size[3],
                            double *loss, float *grad_host, long long count);

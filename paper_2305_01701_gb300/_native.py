@@ -81,6 +81,7 @@ SIGNATURES = [
     ("ep_net_get_params", _I, [_P, C.POINTER(C.c_float), C.c_longlong]),
     ("ep_net_set_params", _I, [_P, C.POINTER(C.c_float), C.c_longlong]),
     ("ep_net_forward", _I, [_P, _P, _I, _IP, _P]),
+    ("ep_net_forward_static", _I, [_P, _P, _I, _IP, _P]),
     ("ep_net_gradients", _I, [_P, _P, _P, _I, _IP, C.POINTER(C.c_double), C.POINTER(C.c_float), C.c_longlong]),
     ("ep_net_train_step", _I, [_P, _P, _P, _I, _IP, C.c_float, C.POINTER(C.c_double)]),
     ("ep_net_destroy", _I, [_P]),
@@ -373,6 +374,12 @@ class Net:
 
     def forward(self, x_ptr, N, size, y_ptr):
         _ncheck(self.h, self._L.ep_net_forward(self.h, x_ptr, N, self._size(size), y_ptr))
+
+    def forward_static(self, x_ptr, N, size, y_ptr):
+        """forward() with the activations in the library's static device
+        array: no allocation, shapes up to the static limit, calls on one
+        device must not overlap on the GPU."""
+        _ncheck(self.h, self._L.ep_net_forward_static(self.h, x_ptr, N, self._size(size), y_ptr))
 
     def gradients(self, x_ptr, t_ptr, N, size):
         n = self.n_params()

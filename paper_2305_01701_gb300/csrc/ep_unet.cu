@@ -18,6 +18,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -549,6 +550,122 @@ static bool shape_ok(const ep_net *n, const int size[3]) {
   return true;
 }
 
+// ---- forward pass that allocates nothing ----------------------------------
+// ep_net_forward_static keeps its activations in one file-scope device array
+// instead of buffers sized on first use.  It exists for callers that must not
+// allocate device memory while they run: a solver loop that applies the warm
+// start between load increments on a device whose memory is already spoken
+// for (the grid's arena and the caller's own allocator pool can hold almost
+// all of it, so a new cudaMalloc may fail), and latency-bound loops, because
+// cudaMalloc and cudaFree synchronise the whole device and stall every other
+// stream.  The array holds EP_NET_STATIC_FLOATS floats; larger shapes are
+// rejected.  Every call on a device shares it, so calls whose kernels overlap
+// on the GPU (different streams without ordering between them) race.  None of
+// it has to start at zero: each activation is written in full before it is
+// read.  The first call on a device looks up the array's address (with that
+// device current); make that first call before any stream capture.
+static __device__ __align__(256) float g_static_act[EP_NET_STATIC_FLOATS];
+
+static std::mutex g_static_mu;
+static float *g_static_ptr[64];
+
+// device address of g_static_act on the current device (set up once)
+static ep_status static_act(ep_net *n, float **out) {
+  int dev = 0;
+  NCK(n, cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return nfail(n, EP_ERR_ARG, "ep_net_forward_static: device ordinal above 63");
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void *p = nullptr;
+    NCK(n, cudaGetSymbolAddress(&p, g_static_act));
+    g_static_ptr[dev] = (float *)p;
+  }
+  *out = g_static_ptr[dev];
+  return EP_OK;
+}
+
+struct Shp {
+  int N, X, Y, Z;
+};
+
+static long long svox(const UNet &u, const Shp &s, int lvl) {
+  long long v = (long long)(s.X >> lvl) * (s.Y >> lvl);
+  if (u.D == 3) v *= (s.Z >> lvl);
+  return v;
+}
+
+// floats the forward's activations take at shape s, with each tensor's
+// offset (in the order of indices()) when off is non-null
+static long long static_layout(const UNet &u, const Shp &s, long long *off) {
+  long long total = 0;
+  int q = 0;
+  auto add = [&](int c, int lvl) {
+    if (off) off[q] = total;
+    ++q;
+    total += ((long long)s.N * c * svox(u, s, lvl) + 63) / 64 * 64;  // 256-byte aligned tensors
+  };
+  for (int l = 0; l < u.levels; ++l) {
+    const int c = u.base << l;
+    add(c, l);
+    add(c, l);
+    if (l < u.levels - 1) add(c, l + 1);
+  }
+  for (int l = u.levels - 2; l >= 0; --l) {
+    const int c = u.base << l, cup = u.base << (l + 1);
+    add(cup + c, l);
+    add(c, l);
+    add(c, l);
+  }
+  return total;
+}
+
+template <int D>
+static void conv_fwd_s(const UNet &u, const Shp &s, const Layer &L, const float *x, float *y, int lvl, int relu) {
+  const long long nv = svox(u, s, lvl);
+  dim3 grid(nblk(nv), (L.cout + 7) / 8, s.N);
+  const int X = s.X >> lvl, Y = s.Y >> lvl, Z = D == 3 ? (s.Z >> lvl) : 1;
+  if (L.k == 3)
+    k_conv<D, 3, false><<<grid, NT, 0, u.st>>>(x, u.wb + L.woff, u.w + L.boff, y, s.N, L.cin, L.cout, X, Y, Z, relu,
+                                               L.cin, L.cout);
+  else
+    k_conv<D, 1, false><<<grid, NT, 0, u.st>>>(x, u.wb + L.woff, u.w + L.boff, y, s.N, L.cin, L.cout, X, Y, Z, relu,
+                                               L.cin, L.cout);
+}
+
+// the network's forward pass with activations at act + off[q] and the head
+// writing straight into y; same kernels and launch shapes as forward()
+template <int D>
+static void forward_static(const UNet &u, const Shp &s, const float *x, float *act, const long long *off, float *y) {
+  const Idx I = indices(u);
+  int li = 0;
+  const float *in = x;
+  for (int l = 0; l < u.levels; ++l) {
+    conv_fwd_s<D>(u, s, u.layers[li++], in, act + off[I.e0[l]], l, 1);
+    conv_fwd_s<D>(u, s, u.layers[li++], act + off[I.e0[l]], act + off[I.e1[l]], l, 1);
+    if (l < u.levels - 1) {
+      const int X = s.X >> l, Y = s.Y >> l, Z = D == 3 ? (s.Z >> l) : 1;
+      const long long n = (long long)s.N * (u.base << l) * svox(u, s, l + 1);
+      k_pool<D><<<nblk(n), NT, 0, u.st>>>(act + off[I.e1[l]], act + off[I.pool[l]], (long long)s.N * (u.base << l),
+                                          X, Y, Z);
+      in = act + off[I.pool[l]];
+    }
+  }
+  const float *prev = act + off[I.e1[u.levels - 1]];
+  for (int l = u.levels - 2; l >= 0; --l) {
+    const int c = u.base << l, cup = u.base << (l + 1);
+    const int X = s.X >> l, Y = s.Y >> l, Z = D == 3 ? (s.Z >> l) : 1;
+    const long long nv = svox(u, s, l);
+    float *cat = act + off[I.cat[l]];
+    k_up<D><<<nblk((long long)s.N * cup * nv), NT, 0, u.st>>>(prev, cat, s.N, cup, cup + c, 0, X, Y, Z);
+    k_slot_copy<<<nblk((long long)s.N * c * nv), NT, 0, u.st>>>(act + off[I.e1[l]], cat, s.N, c, c, 0, cup + c, cup,
+                                                                nv, 0);
+    conv_fwd_s<D>(u, s, u.layers[li++], cat, act + off[I.d0[l]], l, 1);
+    conv_fwd_s<D>(u, s, u.layers[li++], act + off[I.d0[l]], act + off[I.d1[l]], l, 1);
+    prev = act + off[I.d1[l]];
+  }
+  conv_fwd_s<D>(u, s, u.layers[li++], prev, y, 0, 0);
+}
+
 extern "C" {
 
 ep_status ep_net_create(int ndim, int in_ch, int out_ch, int base, int levels, unsigned long long seed, void *stream,
@@ -624,6 +741,28 @@ ep_status ep_net_forward(ep_net *n, const float *x, int N, const int size[3], fl
   if (u.D == 2) forward<2>(u, x); else forward<3>(u, x);
   const long long no = (long long)N * u.cout * vox(u, 0);
   NCK(n, cudaMemcpyAsync(y, u.act[indices(u).out], no * 4, cudaMemcpyDeviceToDevice, u.st));
+  NCK(n, cudaGetLastError());
+  return EP_OK;
+}
+
+// See the declaration in ep.h and the notes above g_static_act.
+ep_status ep_net_forward_static(ep_net *n, const float *x, int N, const int size[3], float *y) {
+  if (!n || !x || !y || N < 1 || !size || !shape_ok(n, size))
+    return nfail(n, EP_ERR_ARG, "ep_net_forward_static: sizes must be multiples of 2^(levels-1)");
+  const UNet &u = n->u;
+  const Shp s{N, size[0], size[1], u.D == 3 ? size[2] : 1};
+  long long off[64];
+  const long long need = static_layout(u, s, off);
+  if (need > EP_NET_STATIC_FLOATS)
+    return nfail(n, EP_ERR_ARG,
+                 "ep_net_forward_static: this shape needs " + std::to_string(need) +
+                     " floats of activations, above the static limit of " +
+                     std::to_string((long long)EP_NET_STATIC_FLOATS) + " (use ep_net_forward)");
+  float *act = nullptr;
+  const ep_status r = static_act(n, &act);
+  if (r != EP_OK) return r;
+  if (u.D == 2) forward_static<2>(u, s, x, act, off, y);
+  else forward_static<3>(u, s, x, act, off, y);
   NCK(n, cudaGetLastError());
   return EP_OK;
 }
