@@ -155,9 +155,10 @@ ep_status ep_get_fields(ep_handle h, int field, double *host_out, size_t count);
 ep_status ep_set_fields(ep_handle h, int field, const double *host_in, size_t count);
 
 /* Sweep kernel selection.  EP_KERNEL_AUTO (default): the fastest measured
- * kernel for the grid -- the fused one-kernel sweep for FP32 2D grids, the
- * staged five-kernel sweep otherwise (FP64 is bound by FP64 arithmetic on
- * GB300, where the staged sweep does no halo recomputation).
+ * kernel for the grid -- for FP32 grids the fused one-kernel sweep (2D) and
+ * the register z-march sweep (3D), for FP64 grids the staged five-kernel
+ * sweep (FP64 is bound by FP64 arithmetic on GB300, where the staged sweep
+ * does no halo recomputation).
  * EP_KERNEL_STAGED / EP_KERNEL_FUSED force one;
  * EP_KERNEL_FUSED_TMA is the 3D fused sweep with every plane streamed by
  * the tensor-memory accelerator (a timed-out copy ends the solve with

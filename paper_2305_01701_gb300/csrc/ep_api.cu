@@ -422,20 +422,29 @@ ep_status prologue(ep_grid *h, const double *const dv[3]) {
   return EP_OK;
 }
 
-// A fused 3D kernel runs only when asked for (without a body force): on
-// GB300 both fused flavours are slower than the staged sweep (they are bound
-// by shared-memory traffic at one block per SM), so AUTO stays staged.
+// The fused 3D kernels serve sweeps without a body force.  AUTO takes the
+// register z-march kernel for FP32 grids (the fastest measured on GB300) and
+// the staged sweep for FP64 ones (bound by FP64 arithmetic, where the staged
+// sweep's lack of halo recomputation wins).
+int fused_variant(const ep_grid *h) {
+  if (h->variant == EP_KERNEL_AUTO)
+    return h->prec == EP_FP32_MIXED ? EP_KERNEL_FUSED_REG : EP_KERNEL_STAGED;
+  return h->variant;
+}
+
 template <typename T>
 bool use_fused(const ep_grid *h) {
   if (h->ndim != 3 || h->have_f) return false;
-  return h->variant == EP_KERNEL_FUSED || h->variant == EP_KERNEL_FUSED_TMA || h->variant == EP_KERNEL_FUSED_REG;
+  const int v = fused_variant(h);
+  return v == EP_KERNEL_FUSED || v == EP_KERNEL_FUSED_TMA || v == EP_KERNEL_FUSED_REG;
 }
 
 // one fused 3D iteration in the grid's chosen flavour
 template <typename T>
 bool launch_fused_any(const ep_grid *h, const Stage<T> &S, const DevInfo *di, cudaStream_t st) {
-  if (h->variant == EP_KERNEL_FUSED_TMA) return launch_fused3d_tma<T>(h->g, S, h->dscal, di, h->kz, st);
-  if (h->variant == EP_KERNEL_FUSED_REG) {
+  const int v = fused_variant(h);
+  if (v == EP_KERNEL_FUSED_TMA) return launch_fused3d_tma<T>(h->g, S, h->dscal, di, h->kz, st);
+  if (v == EP_KERNEL_FUSED_REG) {
     launch_fused3d_reg<T>(h->g, S, h->dscal, di, h->kz, st);
     return true;
   }
@@ -1084,8 +1093,6 @@ ep_status ep_set_kernel(ep_handle h, int variant, int shape) {
     return fail(h, EP_ERR_ARG, "ep_set_kernel: unknown variant");
   if ((variant == EP_KERNEL_FUSED_TMA || variant == EP_KERNEL_FUSED_REG) && h->ndim != 3)
     return fail(h, EP_ERR_ARG, "ep_set_kernel: the TMA and register sweeps are 3D only");
-  if (variant == EP_KERNEL_FUSED_REG && h->g.box >= (1LL << 31))
-    return fail(h, EP_ERR_ARG, "ep_set_kernel: the register sweep indexes with 32 bits (box below 2^31 elements)");
   if (shape >= 0 && h->ndim == 2 && shape > 2)
     return fail(h, EP_ERR_ARG, "ep_set_kernel: shape is z-planes (3D, 0: by grid size) or a tile 0..2 (2D)");
   if (h->chunk) {

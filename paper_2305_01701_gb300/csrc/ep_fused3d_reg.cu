@@ -15,8 +15,7 @@
 //   * inputs arrive through plain coalesced loads issued one plane ahead.
 // Plane t of the march computes spins at plane t, edge trials at face t and
 // plane t-1, centres t-1, edges t-1 and velocities t-2.  Four block barriers
-// separate the steps of a plane.  Indices are 32-bit: the box must hold
-// fewer than 2^31 elements.
+// separate the steps of a plane.
 #include <math.h>
 
 #include "ep_internal.cuh"
@@ -56,25 +55,6 @@ struct Args {
   T *snn[3], *sns[3], *snp, *uo[3];
 };
 
-// per-thread validity of each computed quantity (the parts that do not
-// depend on the plane), one bit each
-enum : unsigned {
-  M_EXY = 1u << 0,   // xy spin / strain rate, xy edge trial
-  M_EXZ = 1u << 1,   // xz spin / strain rate
-  M_EYZ = 1u << 2,   // yz spin / strain rate
-  M_TXZ = 1u << 3,   // xz edge trial
-  M_TYZ = 1u << 4,   // yz edge trial
-  M_CEN = 1u << 5,   // centre trial
-  M_RET = 1u << 6,   // centre return
-  M_NXY = 1u << 7,   // edge deviators
-  M_NXZ = 1u << 8,
-  M_NYZ = 1u << 9,
-  M_VX = 1u << 10,   // velocity components with a residual
-  M_VY = 1u << 11,
-  M_VZ = 1u << 12,
-  M_OUT = 1u << 13,  // a written column
-};
-
 template <typename T, int H>
 __global__ void __launch_bounds__(WX *H, 1)
     k_fused3d_reg(const Args<T> A, Geo g, const Scal *sc, const DevInfo *di, int kz) {
@@ -86,38 +66,16 @@ __global__ void __launch_bounds__(WX *H, 1)
   const int i0 = blockIdx.x * OX, j0 = blockIdx.y * (H - 4);
   const int gi = i0 - 2 + a, gj = j0 - 2 + b;
   const int kb = blockIdx.z * kz, ke = min(kb + kz, g.pz);
-  const int nx = g.nx, ny = g.ny, nz = g.nz;
-  const unsigned pz = (unsigned)g.pz, uplane = (unsigned)g.plane;  // the box has < 2^31 elements
+  const int nx = g.nx, ny = g.ny, nz = g.nz, pz = g.pz;
+  const long long px = g.px, plane = g.plane;
   const bool inb = gi >= 0 && gi < g.px && gj >= 0 && gj < g.py;
-  const unsigned col = inb ? (unsigned)gj * (unsigned)g.px + (unsigned)gi : 0u;  // offset in a plane
+  const long long col = inb ? (long long)gj * px + gi : 0;  // this column's offset in a plane
+  const bool out_col = a >= 2 && a < W - 2 && b >= 2 && b < H - 2;
   const T rdx = (T)g.rdx, rdy = (T)g.rdy, rdz = (T)g.rdz;
   const T two_eta = (T)sc->two_eta, bt = (T)sc->bt, ob = (T)1 - bt;
   const T bp = (T)sc->bp, obp = (T)1 - bp, KDt = (T)sc->KDt, Acoef = (T)sc->A;
   const T vs = (T)sc->vstep, qr = (T)0.25, third = (T)(1.0 / 3.0), hf = (T)0.5;
   const int rb = b + 1;  // this thread's row in a Rows slot
-
-  unsigned m = 0;
-  {
-    const bool xi1 = gi >= 1 && gi <= nx - 1, xi0 = gi >= 0 && gi < nx;
-    const bool yj1 = gj >= 1 && gj <= ny - 1, yj0 = gj >= 0 && gj < ny;
-    const bool inner = a >= 2 && a < W - 1 && b >= 2 && b < H - 1;
-    const bool out_col = a >= 2 && a < W - 2 && b >= 2 && b < H - 2;
-    if (a >= 1 && b >= 1 && xi1 && yj1) m |= M_EXY;
-    if (a >= 1 && xi1 && yj0) m |= M_EXZ;
-    if (b >= 1 && xi0 && yj1) m |= M_EYZ;
-    if (a >= 1 && b < H - 1 && xi1 && yj0) m |= M_TXZ;
-    if (a < W - 1 && b >= 1 && xi0 && yj1) m |= M_TYZ;
-    if (a < W - 1 && b < H - 1 && xi0 && yj0) m |= M_CEN;
-    if (a >= 1 && a < W - 1 && b >= 1 && b < H - 1 && xi0 && yj0) m |= M_RET;
-    if (inner && xi1 && yj1) m |= M_NXY;
-    if (inner && xi1 && yj0) m |= M_NXZ;
-    if (inner && xi0 && yj1) m |= M_NYZ;
-    if (xi1 && gj < ny) m |= M_VX;
-    if (yj1 && gi < nx) m |= M_VY;
-    if (gi < nx && gj < ny) m |= M_VZ;
-    if (out_col && inb) m |= M_OUT;
-  }
-  auto has = [&](unsigned bit) { return (m & bit) != 0u; };
 
   // zero the pad rows (never written afterwards)
   {
@@ -126,12 +84,12 @@ __global__ void __launch_bounds__(WX *H, 1)
     for (int q = threadIdx.x; q < n_rows * 2 * WX; q += WX * H) {
       const int slot = q / (2 * WX), rem = q % (2 * WX);
       const int row = rem < WX ? 0 : H + 1;
-      base[slot * (H + 2) * WX + row * WX + (rem % WX)] = (T)0;
+      base[(long long)slot * (H + 2) * WX + row * WX + (rem % WX)] = (T)0;
     }
   }
 
   auto ld = [&](const T *p, int lev) -> T {
-    return (inb && (unsigned)lev < pz) ? __ldg(p + ((unsigned)lev * uplane + col)) : (T)0;
+    return (inb && lev >= 0 && lev < pz) ? __ldg(p + (long long)lev * plane + col) : (T)0;
   };
 
   // inputs of the next plane (loaded one plane ahead)
@@ -148,6 +106,7 @@ __global__ void __launch_bounds__(WX *H, 1)
     n_soxy = ld(A.sos[0], c); n_tbxy = ld(A.tbs[0], c); n_sop = ld(A.sop, c); n_pb = ld(A.pb, c);
     n_yc = ld(A.yc, c);
   };
+
   // plane history (suffix: _1 plane t-1, _2 plane t-2, _3 plane t-3)
   T u0 = 0, u1 = 0, u2 = 0, u0_1 = 0, u1_1 = 0, u2_1 = 0, u0_2 = 0, u1_2 = 0, u2_2 = 0;
   T rq0 = 0, rq1 = 0, rq2 = 0, rd0 = 0, rd1 = 0, rq0_1 = 0, rq1_1 = 0, rq2_1 = 0, rd0_1 = 0, rd1_1 = 0;
@@ -157,15 +116,9 @@ __global__ void __launch_bounds__(WX *H, 1)
   T sxx_2 = 0, syy_2 = 0, szz_2 = 0, szz_3 = 0;  // centre stress minus pressure
   T nxy_2 = 0, nxz_2 = 0, nyz_2 = 0;           // edge stress, level t-2
 
-  // one plane of the march
-  auto step = [&](const int t) {
+  prefetch(kb - 2);
+  for (int t = kb - 2; t < ke + 2; ++t) {
     const int sl = t & 1, sl1 = sl ^ 1;  // plane slots of t and t - 1
-    const int lc = t - 1, lu = t - 2;
-    const bool tz0 = t >= 0 && t < nz, tz1 = t >= 1 && t <= nz - 1;
-    const bool lc0 = lc >= 0 && lc < nz, lc1 = lc >= 1 && lc <= nz - 1, lco = lc >= kb && lc < ke;
-    const bool lu0 = lu < nz, lu1 = lu >= 1 && lu <= nz - 1, luo = lu >= kb && lu < ke;
-    const bool more = t + 1 < ke + 2;
-
     // ---- 0. take this plane's inputs, publish the row-exchanged ones ----
     u0_2 = u0_1; u1_2 = u1_1; u2_2 = u2_1;
     u0_1 = u0; u1_1 = u1; u2_1 = u2;
@@ -175,7 +128,7 @@ __global__ void __launch_bounds__(WX *H, 1)
     const T soxz = n_soxz, soyz = n_soyz, tbxz = n_tbxz, tbyz = n_tbyz;
     const T son0 = n_son0, son1 = n_son1, son2 = n_son2, tbn0 = n_tbn0, tbn1 = n_tbn1, tbn2 = n_tbn2;
     const T soxy = n_soxy, tbxy = n_tbxy, sop = n_sop, pb = n_pb, yc = n_yc;
-    if (more) prefetch(t + 1);
+    if (t + 1 < ke + 2) prefetch(t + 1);
     S.u0.r[rb][a] = u0; S.u2.r[rb][a] = u2; S.u1[sl].r[rb][a] = u1;
     S.rq0[sl].r[rb][a] = rq0; S.rq1[sl].r[rb][a] = rq1; S.rq2.r[rb][a] = rq2;
     S.rd0[sl].r[rb][a] = rd0; S.rd1[sl].r[rb][a] = rd1;
@@ -186,15 +139,15 @@ __global__ void __launch_bounds__(WX *H, 1)
     {
       const T u0_ym = S.u0.r[rb - 1][a], u2_ym = S.u2.r[rb - 1][a];
       const T u1_xm = xm(u1), u2_xm = xm(u2);
-      if (tz0 && has(M_EXY)) {
+      if (a >= 1 && b >= 1 && t >= 0 && t < nz && gi >= 1 && gi <= nx - 1 && gj >= 1 && gj <= ny - 1) {
         const T x = (u0 - u0_ym) * rdy, y = (u1 - u1_xm) * rdx;
         exy = hf * (x + y); oxy = hf * (x - y);
       }
-      if (tz1 && has(M_EXZ)) {
+      if (a >= 1 && t >= 1 && t <= nz - 1 && gi >= 1 && gi <= nx - 1 && gj >= 0 && gj < ny) {
         const T x = (u0 - u0_1) * rdz, y = (u2 - u2_xm) * rdx;
         exz = hf * (x + y); oxz = hf * (x - y);
       }
-      if (tz1 && has(M_EYZ)) {
+      if (b >= 1 && t >= 1 && t <= nz - 1 && gi >= 0 && gi < nx && gj >= 1 && gj <= ny - 1) {
         const T x = (u1 - u1_1) * rdz, y = (u2 - u2_ym) * rdy;
         eyz = hf * (x + y); oyz = hf * (x - y);
       }
@@ -205,6 +158,7 @@ __global__ void __launch_bounds__(WX *H, 1)
     __syncthreads();
 
     // ---- 2. relaxed trials: faces t (xz, yz), plane t-1 (xy, centres) ----
+    const int lc = t - 1;
     T tsxz = 0, tsyz = 0, tsxy = 0, c0v = 0, c1v = 0, c2v = 0, exx = 0, eyy = 0, ezz = 0;
     {
       // shuffles run on every lane, outside the validity branches
@@ -227,7 +181,7 @@ __global__ void __launch_bounds__(WX *H, 1)
       const T pxz_1_xp = xp(pxz_1), pxz_xp = xp(pxz);
       const T pyz_1_yp = S.pyz[sl1].r[rb + 1][a], pyz_yp = S.pyz[sl].r[rb + 1][a];
 
-      if (tz1 && has(M_TXZ)) {
+      if (a >= 1 && b < H - 1 && t >= 1 && t <= nz - 1 && gi >= 1 && gi <= nx - 1 && gj >= 0 && gj < ny) {
         const T dzx = qr * (rd1_1_xm + rd1_1 + rd1_xm + rd1);
         const T Tyz = qr * (rq2_xm + rq2 + rq2_yp_xm + rq2_yp);
         const T Wyz = qr * (oyz_xm + oyz + oyz_yp_xm + oyz_yp);
@@ -236,7 +190,7 @@ __global__ void __launch_bounds__(WX *H, 1)
         const T tr = tbxz + two_eta * exz + (oxz * dzx + Tyz * Wxy - Txy * Wyz);
         tsxz = bt * soxz + ob * tr;
       }
-      if (tz1 && has(M_TYZ)) {
+      if (a < W - 1 && b >= 1 && t >= 1 && t <= nz - 1 && gi >= 0 && gi < nx && gj >= 1 && gj <= ny - 1) {
         const T dzy = qr * ((rd1_1_ym - rd0_1_ym) + (rd1_1 - rd0_1) + (rd1_ym - rd0_ym) + (rd1 - rd0));
         const T Txy = qr * (rq0_1 + rq0_1_xp + rq0 + rq0_xp);
         const T Wxy = qr * (oxy_1 + oxy_1_xp + oxy + oxy_xp);
@@ -245,7 +199,7 @@ __global__ void __launch_bounds__(WX *H, 1)
         const T tr = tbyz + two_eta * eyz + (oyz * dzy - Txy * Wxz - Txz * Wxy);
         tsyz = bt * soyz + ob * tr;
       }
-      if (lc0 && has(M_EXY)) {
+      if (a >= 1 && b >= 1 && lc >= 0 && lc < nz && gi >= 1 && gi <= nx - 1 && gj >= 1 && gj <= ny - 1) {
         const T dyx = qr * (rd0_1_ym_xm + rd0_1_ym + rd0_1_xm + rd0_1);
         const T Tyz = qr * (rq2_1_xm + rq2_1 + rq2_xm + rq2);
         const T Wyz = qr * (oyz_1_xm + oyz_1 + oyz_xm + oyz);
@@ -254,7 +208,7 @@ __global__ void __launch_bounds__(WX *H, 1)
         const T tr = tbxy + two_eta * exy_1 + (oxy_1 * dyx + Tyz * Wxz + Txz * Wyz);
         tsxy = bt * soxy + ob * tr;
       }
-      if (lc0 && has(M_CEN)) {
+      if (a < W - 1 && b < H - 1 && lc >= 0 && lc < nz && gi >= 0 && gi < nx && gj >= 0 && gj < ny) {
         exx = (u0_1_xp - u0_1) * rdx;
         eyy = (u1_1_yp - u1_1) * rdy;
         ezz = (u2 - u2_1) * rdz;
@@ -280,7 +234,8 @@ __global__ void __launch_bounds__(WX *H, 1)
       const T tsxy_yp_xp = xp(tsxy_yp);
       const T tsxz_1_xp = xp(tsxz_1), tsxz_xp = xp(tsxz);
       const T tsyz_1_yp = S.tsyz[sl1].r[rb + 1][a], tsyz_yp = S.tsyz[sl].r[rb + 1][a];
-      if (lc0 && has(M_RET)) {
+      if (a >= 1 && a < W - 1 && b >= 1 && b < H - 1 && lc >= 0 && lc < nz && gi >= 0 && gi < nx && gj >= 0 &&
+          gj < ny) {
         const T div = exx + eyy + ezz;
         const T pr = bp * sop + obp * (pb - KDt * div);
         const T txy = qr * (tsxy + tsxy_xp + tsxy_yp + tsxy_yp_xp);
@@ -293,8 +248,8 @@ __global__ void __launch_bounds__(WX *H, 1)
         s_1 = sj > Y ? Y / sj : (T)1;
         const T n0 = s_1 * c0v, n1 = s_1 * c1v, n2 = s_1 * c2v;
         sxx_1 = n0 - pr; syy_1 = n1 - pr; szz_1 = n2 - pr;
-        if (lco && has(M_OUT)) {
-          const unsigned ec = (unsigned)lc * uplane + col;
+        if (out_col && lc >= kb && lc < ke) {
+          const long long ec = (long long)lc * plane + col;
           A.snn[0][ec] = n0; A.snn[1][ec] = n1; A.snn[2][ec] = n2; A.snp[ec] = pr;
         }
       }
@@ -308,11 +263,15 @@ __global__ void __launch_bounds__(WX *H, 1)
       const T s_1_xm = xm(s_1), s_2_xm = xm(s_2);
       const T s_1_ym = S.s[sl1].r[rb - 1][a], s_2_ym = S.s[sl].r[rb - 1][a];
       const T s_1_ym_xm = xm(s_1_ym);
-      if (lc0 && has(M_NXY)) nxy_1 = qr * (s_1_ym_xm + s_1_ym + s_1_xm + s_1) * tsxy;
-      if (lc1 && has(M_NXZ)) nxz_1 = qr * (s_2_xm + s_2 + s_1_xm + s_1) * tsxz_1;
-      if (lc1 && has(M_NYZ)) nyz_1 = qr * (s_2_ym + s_2 + s_1_ym + s_1) * tsyz_1;
-      if (lco && has(M_OUT)) {
-        const unsigned e = (unsigned)lc * uplane + col;
+      const bool inner = a >= 2 && a < W - 1 && b >= 2 && b < H - 1;
+      if (inner && lc >= 0 && lc < nz && gi >= 1 && gi <= nx - 1 && gj >= 1 && gj <= ny - 1)
+        nxy_1 = qr * (s_1_ym_xm + s_1_ym + s_1_xm + s_1) * tsxy;
+      if (inner && lc >= 1 && lc <= nz - 1 && gi >= 1 && gi <= nx - 1 && gj >= 0 && gj < ny)
+        nxz_1 = qr * (s_2_xm + s_2 + s_1_xm + s_1) * tsxz_1;
+      if (inner && lc >= 1 && lc <= nz - 1 && gi >= 0 && gi < nx && gj >= 1 && gj <= ny - 1)
+        nyz_1 = qr * (s_2_ym + s_2 + s_1_ym + s_1) * tsyz_1;
+      if (out_col && lc >= kb && lc < ke && inb) {
+        const long long e = (long long)lc * plane + col;
         A.sns[0][e] = nxy_1; A.sns[1][e] = nxz_1; A.sns[2][e] = nyz_1;
       }
     }
@@ -320,25 +279,26 @@ __global__ void __launch_bounds__(WX *H, 1)
 
     // ---- 5. residual and velocity update of plane t-2 ----
     {
+      const int lu = t - 2;
       const T sxx_2_xm = xm(sxx_2), nxy_2_xp = xp(nxy_2), nxz_2_xp = xp(nxz_2);
-      if (luo && has(M_OUT)) {
+      if (out_col && inb && lu >= kb && lu < ke) {
         const T nxy_2_yp = S.nxy[sl].r[rb + 1][a], syy_2_ym = S.syy[sl].r[rb - 1][a];
         const T nyz_2_yp = S.nyz[sl].r[rb + 1][a];
-        const unsigned e = (unsigned)lu * uplane + col;
+        const long long e = (long long)lu * plane + col;
         T un = u0_2;
-        if (lu0 && has(M_VX)) {
+        if (gi >= 1 && gi <= nx - 1 && gj < ny && lu < nz) {
           const T R = (sxx_2 - sxx_2_xm) * rdx + (nxy_2_yp - nxy_2) * rdy + (nxz_1 - nxz_2) * rdz;
           un = u0_2 + vs * R;
         }
         A.uo[0][e] = un;
         un = u1_2;
-        if (lu0 && has(M_VY)) {
+        if (gj >= 1 && gj <= ny - 1 && gi < nx && lu < nz) {
           const T R = (syy_2 - syy_2_ym) * rdy + (nxy_2_xp - nxy_2) * rdx + (nyz_1 - nyz_2) * rdz;
           un = u1_2 + vs * R;
         }
         A.uo[1][e] = un;
         un = u2_2;
-        if (lu1 && has(M_VZ)) {
+        if (lu >= 1 && lu <= nz - 1 && gi < nx && gj < ny) {
           const T R = (szz_2 - szz_3) * rdz + (nxz_2_xp - nxz_2) * rdx + (nyz_2_yp - nyz_2) * rdy;
           un = u2_2 + vs * R;
         }
@@ -353,10 +313,7 @@ __global__ void __launch_bounds__(WX *H, 1)
     s_2 = s_1;
     sxx_2 = sxx_1; syy_2 = syy_1; szz_3 = szz_2; szz_2 = szz_1;
     nxy_2 = nxy_1; nxz_2 = nxz_1; nyz_2 = nyz_1;
-  };
-
-  prefetch(kb - 2);
-  for (int t = kb - 2; t < ke + 2; ++t) step(t);
+  }
 }
 
 template <typename T>
