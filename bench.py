@@ -50,6 +50,15 @@ def parse():
     ap.add_argument("--increment", type=int, default=5, help="load increment that is timed")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-fp64", action="store_true", help="skip timing the plain FP64 solve")
+    ap.add_argument("--warm", action="store_true", help="also train the warm-start network and time a warm increment")
+    ap.add_argument("--warm-increment", type=int, default=7, help="increment timed with and without the warm start")
+    ap.add_argument("--warm-train", type=int, default=2, help="held-out setups whose trajectories train the network")
+    ap.add_argument("--warm-steps", type=int, default=150, help="training steps")
+    ap.add_argument("--warm-base", type=int, default=32, help="base channels of the network")
+    ap.add_argument("--batch", type=int, default=0, help="time the batched 2D solve of this many instances")
+    ap.add_argument("--batch-increment", type=int, default=2, help="batched increment that is timed")
+    ap.add_argument("--batch-nchk", type=int, default=1000,
+                    help="check interval of the batched FP32 solve (the FP32 stopping test needs long intervals)")
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-size", type=int, default=24)
@@ -78,7 +87,9 @@ class Clocks:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_%d.csv" % index)
+        # the samples go to $EP_CLOCKS_DIR (default: the system temporary directory)
+        import tempfile
+        self.path = os.path.join(os.environ.get("EP_CLOCKS_DIR", tempfile.gettempdir()), "clocks_%d.csv" % index)
 
     def start(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
@@ -156,7 +167,10 @@ def oracle_increment_rate(size, tol, increment, max_seconds=30.0):
 
 
 def alg_bytes_per_cell(ndim, precision):
-    """Bytes one fused sweep iteration must move per cell."""
+    """Bytes one fused sweep iteration must move per cell: it reads the
+    velocity increment, the stress state and pressure, the base trial and
+    base pressure, B c and the rotation weights, and writes the velocity
+    increment, the stress state and pressure."""
     nd, ns = ndim, (3 if ndim == 3 else 1)
     words = (nd + (nd + ns) + 1 + (nd + ns) + 1 + 1 + (ns + nd - 1)) + (nd + (nd + ns) + 1)
     return words * (8 if precision == "fp64" else 4)
@@ -320,6 +334,12 @@ def our_arm(args):
                 "fp32_speedup": t64 * 1e3 / ms_per_step}
         g64.close()
 
+    warm = None
+    if args.warm:
+        warm = warm_arm(args, torch, P, stream, barrier, s, cells)
+        if fp64 is not None and args.warm_increment == args.increment:
+            warm["fp64_plain_ms"] = fp64["ms_per_increment"]
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         per_inc, c_iters, c_cells = oracle_increment_rate(args.cpu_size, args.tol, args.increment)
@@ -360,6 +380,7 @@ def our_arm(args):
         "roofline": roof,
         "e2e": e2e,
         "fp64_plain": fp64,
+        "warm_start": warm,
         "cpu_baseline": cpu,
     }
     if rank == 0:
@@ -369,10 +390,178 @@ def our_arm(args):
     return 0
 
 
+def warm_arm(args, torch, P, stream, barrier, s, cells):
+    """The learned warm start on the benchmark box: a 3D U-Net (3 levels,
+    BF16 weights, FP32 accumulation) trained on the GPU with the library's
+    kernels from trajectories of held-out seeds of the same setup, then the
+    increment `--warm-increment` solved from one device checkpoint with the
+    plain start and with the network's start (FP32 sweeps, same tolerance)."""
+    import time as _t
+    import ep_inputs as E
+    from paper_2305_01701_gb300 import warmstart as W
+
+    t_train0 = _t.perf_counter()
+    net = W.new_net(3, base=args.warm_base, levels=3, seed=7, stream=stream.cuda_stream)
+    incs = args.warm_increment + 1
+    groups = []
+    for q in range(args.warm_train):
+        ts = E.config(5, n=s.n, tol=s.tol, seed=s.seed + 101 + q, c0=s.c0 * (1.0 + 0.05 * (q + 1)))
+        gt = make_grid(P, ts, "fp32", args.kernel, stream.cuda_stream)
+        data = W.Samples(3, gt.warm_dims(), capacity=incs)
+        W.collect(gt, ts.a, ts.dt, incs, data, load_plane=P.LOAD_XZ)
+        gt.close()
+        groups.append(data)
+    losses = W.train(net, groups, steps=args.warm_steps, lr=1e-3, batch=2)
+    torch.cuda.synchronize()
+    t_train = _t.perf_counter() - t_train0
+
+    g = prepare(P, s, "fp32", args.warm_increment, args.kernel, stream.cuda_stream)
+    g.attach_warm_start(net)
+
+    def one(warm):
+        g.restore()
+        g.apply_increment(s.a, s.dt, P.LOAD_XZ, use_warm_start=warm)
+        return g.solve_increment()
+
+    one(False)
+    one(True)
+    res = {}
+    for warm in (False, True):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        ev0.record(stream)
+        info = one(warm)
+        ev1.record(stream)
+        barrier()
+        res[warm] = (ev0.elapsed_time(ev1), info)
+    bpc = g.sweep_bytes_per_cell()
+    out = {"increment": args.warm_increment,
+           "plain_ms": res[False][0], "plain_iterations": res[False][1]["iters"],
+           "warm_ms": res[True][0], "warm_iterations": res[True][1]["iters"],
+           "warm_GB_per_s": bpc * cells * res[True][1]["iters"] / (res[True][0] * 1e-3) / 1e9,
+           "net": "3-level U-Net, base %d, BF16 weights, FP32 accumulation" % args.warm_base,
+           "training": {"setups": args.warm_train, "samples": sum(d.n for d in groups), "steps": args.warm_steps,
+                        "first_loss": float(losses[0]), "last_loss": float(sum(losses[-10:]) / 10),
+                        "seconds": t_train}}
+    g.close()
+    net.close()
+    return out
+
+
+def batch_arm(args):
+    """Config 4: uneven 2D instances advanced by one persistent, graph-captured
+    launch per iteration (FP32 sweeps, FP64 norms and history).  One step is
+    one batched increment (`--batch-increment`) re-solved from a device
+    checkpoint of every instance."""
+    import torch
+    import ep_inputs as E
+    import paper_2305_01701_gb300 as P
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    setups = E.batch_setups(args.batch)
+    grids = []
+    for s in setups:
+        g = P.Grid(2, s.n, precision=P.FP32_MIXED, stream=stream.cuda_stream)
+        g.set_material(s.K, s.G, s.mu_s, s.phi_deg, s.psi_deg, s.cohesion())
+        g.set_solver(tol=s.tol, max_iter=2000000, n_chk=args.batch_nchk)
+        grids.append(g)
+    B = P.Batch(grids)
+    a, dt = setups[0].a, setups[0].dt
+    for inc in range(1, args.batch_increment):
+        B.apply_increment(a, dt)
+        B.solve_increment()
+    for g in grids:
+        g.snapshot()
+
+    def step():
+        for g in grids:
+            g.restore()
+        B.apply_increment(a, dt)
+        return B.solve_increment()[0]
+
+    B.apply_increment(a, dt)
+    tile = B.autotune(20)                  # restarts the open increments
+    B.solve_increment()
+    for _ in range(args.warmup):
+        step()
+
+    def barrier():
+        torch.cuda.synchronize()
+
+    clk = Clocks(local)
+    clk.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0.record(stream)
+    infos = [step() for _ in range(args.steps)]
+    ev1.record(stream)
+    barrier()
+    clocks = clk.stop()
+    sec = ev0.elapsed_time(ev1) * 1e-3
+    bpc = grids[0].sweep_bytes_per_cell()
+    cells = [s.n[0] * s.n[1] for s in setups]
+    moved = sum(bpc * c * i["iters"] for inf in infos for c, i in zip(cells, inf))
+    gbs = moved / sec / 1e9
+    iters = [i["iters"] for i in infos[-1]]
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle as O
+        import time as _t
+        small = [q for q in setups if q.n[0] == min(x.n[0] for x in setups)][0]
+        o = O.from_setup(small)
+        o.set_solver(tol=small.tol, max_iter=2000000, n_chk=100)
+        for _ in range(args.batch_increment - 1):
+            o.apply_increment([a, -a, 0.0], dt)
+            o.solve_increment()
+        t0 = _t.perf_counter()
+        o.apply_increment([a, -a, 0.0], dt)
+        oi = o.solve_increment()
+        ot = _t.perf_counter() - t0
+        ocells = small.n[0] * small.n[1]
+        cpu = {"value": alg_bytes_per_cell(2, "fp64") * ocells * max(oi["iters"], 1) / ot / 1e9, "unit": "GB/s",
+               "cores": 1, "kind": "oracle",
+               "sample": "increment %d of one %dx%d instance (%s), single-threaded FP64 oracle, %d iterations "
+                         "in %.2f s" % (args.batch_increment, small.n[0], small.n[1], small.name, oi["iters"], ot)}
+    line = {
+        "metric": "aggregate sweep GB/s and wall time per batched increment to tol 1e-6",
+        "value": gbs, "unit": "GB/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": sec / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "2d-batch %d instances of {127,255,383,511}^2, increment %d, tol 1e-6, fp32 sweeps"
+                   % (len(setups), args.batch_increment),
+                   "cells": sum(cells), "tile": tile, "iterations_min_max": [min(iters), max(iters)],
+                   "iterations_sum": sum(iters),
+                   "l2": "inputs larger than L2 while most instances iterate (%.1f GB per iteration)"
+                         % (bpc * sum(cells) / 1e9)},
+        "clocks": clocks,
+        "roofline": {"bound": "hbm", "kernel": "k_fused2d (whole batched solve, check iterations included)",
+                     "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                     "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6800 GB/s",
+                     "traffic": None, "alg_bytes_per_cell": bpc},
+        "gpu_launches": None,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+    B.close()
+    for g in grids:
+        g.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.batch > 0:
+        return batch_arm(args)
     return our_arm(args)
 
 

@@ -38,7 +38,7 @@ class Info(C.Structure):
                 ("eps_tau", C.c_double), ("eps_p", C.c_double), ("eps_rel", C.c_double),
                 ("max_r", C.c_double), ("max_sigma", C.c_double), ("n_plastic", C.c_long),
                 ("sxx_int_centre", C.c_double), ("sxx_int_right", C.c_double),
-                ("status", C.c_int)]
+                ("status", C.c_int), ("frozen_at", C.c_long)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -69,6 +69,7 @@ def lib():
         L.or_destroy.argtypes = [P]
         L.or_set_material.argtypes = [P, D, D, D, D, D, DP]
         L.or_set_solver.argtypes = [P, D, Lg, I, D, D, D, I]
+        L.or_set_freeze.argtypes = [P, Lg, D]
         L.or_apply_increment.argtypes = [P, DP, D, DP]
         L.or_solve_increment.argtypes = [P, C.POINTER(Info)]
         L.or_commit.argtypes = [P]
@@ -140,6 +141,11 @@ class Oracle:
             c_cfl = 0.9 / math.sqrt(self.ndim)
         self._chk(self.L_.or_set_solver(self.h, tol, int(max_iter), int(n_chk), c_cfl, xi, r_pt,
                                         int(jaumann)), "set_solver")
+
+    def set_freeze(self, freeze_iter, freeze_eps=1e-4):
+        """Frozen plasticity (Sec. 3.3): freeze the centre return scales at the
+        first check with k >= freeze_iter and eps_rel > freeze_eps (0: never)."""
+        self._chk(self.L_.or_set_freeze(self.h, int(freeze_iter), float(freeze_eps)), "set_freeze")
 
     def apply_increment(self, rates, dt, body_force=None):
         r = np.ascontiguousarray(list(rates) + [0.0] * (3 - len(rates)), dtype=np.float64)

@@ -20,7 +20,7 @@
  *   L-infinity convergence norms .... Eqs. Convergence1-3
  *   history commit .................. the "old" fields of Fig. 1
  *
- * Readings where the paper is silent or garbled (each listed in the design doc):
+ * Readings where the paper is silent or garbled:
  *  - J2 squares its shear terms (the printed 2D/3D formulas drop the squares);
  *  - 2D carries no tau_zz and uses J2 = (txx^2 + tyy^2)/2 + txy^2;
  *  - spin w_xy = (dvx/dy - dvy/dx)/2, the textbook Jaumann sign;
@@ -69,6 +69,7 @@ typedef struct {
   long n_plastic;
   double sxx_int_centre, sxx_int_right;
   int status;
+  long frozen_at;   /* iteration at which the return scales were frozen, -1 if never */
 } or_info;
 
 typedef struct {
@@ -82,6 +83,11 @@ typedef struct {
   double tol, c_cfl, xi, r_pt;
   long max_iter;
   int n_chk, jaumann;
+  /* frozen plasticity (Sec. 3.3): from the first check at k >= freeze_iter
+   * with eps_rel > freeze_eps on, the centre scales s keep their values */
+  long freeze_iter;   /* 0: never */
+  double freeze_eps;
+  int frozen;
   /* loading of the current increment (Eqs. A7-A9M) */
   double rate[3], dt;
   double *f[3];
@@ -149,6 +155,7 @@ or_grid *or_create(int ndim, const int *n, const double *L) {
   g->L[0] = L[0]; g->L[1] = L[1]; g->L[2] = ndim == 3 ? L[2] : 1.0;
   g->dx = g->L[0] / g->nx; g->dy = g->L[1] / g->ny; g->dz = g->L[2] / g->nz;
   g->tol = 1e-8; g->max_iter = 1000000; g->n_chk = 100;
+  g->freeze_iter = 0; g->freeze_eps = 1e-4; g->frozen = 0;
   g->c_cfl = 0.9 / sqrt((double)ndim); g->xi = 1.0; g->r_pt = 0.5; g->jaumann = 1;
   long nc = n_centres(g);
   g->coh = zalloc(nc); g->p = zalloc(nc); g->epl = zalloc(nc); g->div = zalloc(nc);
@@ -209,6 +216,20 @@ int or_set_solver(or_grid *g, double tol, long max_iter, int n_chk, double c_cfl
     return OR_ERR_ARG;
   g->tol = tol; g->max_iter = max_iter; g->n_chk = n_chk; g->c_cfl = c_cfl; g->xi = xi; g->r_pt = r_pt;
   g->jaumann = jaumann != 0;
+  return OR_OK;
+}
+
+/* Frozen plasticity (Sec. 3.3, last paragraph): the paper stops updating the
+ * plastic multiplier when an increment still has eps_rel > 1e-4 after
+ * 16 n_x iterations and iterates the then-linear problem to tolerance.  Here:
+ * at the first check with k >= freeze_iter and eps_rel > freeze_eps, the
+ * centre scales s of that iteration are kept for the rest of the increment
+ * (edges keep using the mean of their adjacent centre scales).  freeze_iter
+ * = 0 never freezes. */
+int or_set_freeze(or_grid *g, long freeze_iter, double freeze_eps) {
+  if (freeze_iter < 0 || !(freeze_eps >= 0.0)) return OR_ERR_ARG;
+  g->freeze_iter = freeze_iter;
+  g->freeze_eps = freeze_eps;
   return OR_OK;
 }
 
@@ -455,7 +476,7 @@ static void pt_stress(or_grid *g, double bt, double bp) {
     double sj = sqrt(J2);
     double Y = g->A * g->pc[c] + g->B * g->coh[c];
     if (Y < 0.0) Y = 0.0;
-    g->s[c] = sj > Y ? Y / sj : 1.0;
+    if (!g->frozen) g->s[c] = sj > Y ? Y / sj : 1.0;
     for (int d = 0; d < g->ndim; ++d) g->sn[d][c] = g->s[c] * g->Tn[d][c];
   }
   /* vertices / edges: arithmetic mean of the adjacent centre scales */
@@ -660,7 +681,10 @@ static void diagnostics(or_grid *g, or_info *info) {
  *      over the check interval as eps_rel takes V - V^it, Eq. Convergence2),
  *      eps_res = the largest; stop when eps_res <= tol, keeping
  *      (v_k, tau_{k+1}, p_{k+1});
- *   4. v_{k+1} = v_k + R_k / rho~ at interior faces (Eq. A22P). */
+ *   4. v_{k+1} = v_k + R_k / rho~ at interior faces (Eq. A22P).
+ * With frozen plasticity enabled, a check that does not stop and has
+ * k >= freeze_iter and eps_rel > freeze_eps freezes the centre scales s of
+ * iteration k for all later iterations of the increment. */
 int or_solve_increment(or_grid *g, or_info *info) {
   if (!g->in_increment) return OR_ERR_STATE;
   memset(info, 0, sizeof(*info));
@@ -677,6 +701,8 @@ int or_solve_increment(or_grid *g, or_info *info) {
   const double dxm = dx_min(g);
   int status = OR_ERR_NOT_CONVERGED;
   long k_prev = -1;
+  g->frozen = 0;
+  info->frozen_at = -1;
   for (long k = 0;; ++k) {
     evaluate(g, g->vi, q.beta_tau, q.beta_p);
     if (k % g->n_chk == 0 || k == g->max_iter) {
@@ -710,6 +736,10 @@ int or_solve_increment(or_grid *g, or_info *info) {
       if (mr != mr || er != er) { status = OR_ERR_DIVERGED; break; }
       if (er <= g->tol) { status = OR_OK; break; }
       if (k >= g->max_iter) break;
+      if (!g->frozen && g->freeze_iter > 0 && k >= g->freeze_iter && info->eps_rel > g->freeze_eps) {
+        g->frozen = 1;
+        info->frozen_at = k;
+      }
     }
     /* accept the new stress state and update interior velocities (A22P) */
     accept_stress(g);
@@ -722,6 +752,7 @@ int or_solve_increment(or_grid *g, or_info *info) {
       }
     }
   }
+  g->frozen = 0;   /* the scales of this solve stay in g->s for the commit */
   info->status = status;
   diagnostics(g, info);
   return status;

@@ -557,3 +557,90 @@ def test_pt_parameters_follow_the_paper():
     assert bt == pytest.approx((1 / (2 * Gt)) / (1 / (2 * Gt) + 1 / (2 * eta)), rel=1e-14)
     assert bp == pytest.approx((1 / Kt) / (1 / Kt + 1 / (K * 1e-4)), rel=1e-14)
     assert vs == pytest.approx(1 / rho, rel=1e-14)
+
+
+# ------------------------------------------------------- frozen plasticity ----
+def _plastic_tiny_2d(n=(8, 6), c0=2.5e-4, **solver):
+    s = E.Setup("frozen-tiny", 2, n, c0=c0, inclusion_radius=0.3, noise=0.05, seed=77, tol=1e-13)
+    o = O.from_setup(s, jaumann=False, **solver)
+    return s, o
+
+
+def test_frozen_plasticity_is_inert_without_plastic_cells():
+    """Freezing the scales of an increment in which no cell yields (s = 1
+    everywhere) changes nothing: the same iterations and the same fields."""
+    s = E.config(1, n=(12, 10))
+    n = s.n
+    a = O.from_setup(s, tol=1e-11, n_chk=10)
+    b = O.from_setup(s, tol=1e-11, n_chk=10)
+    b.set_freeze(1, 0.0)                         # freeze at the first check after k = 0
+    rates = [1.0, -0.5]
+    for _ in range(2):
+        for o in (a, b):
+            o.apply_increment(rates, s.dt)
+            # a zero interior start, so that the increment iterates
+            vx, vy = o.get("v0x").copy(), o.get("v0y").copy()
+            vx[:, 1:-1] = 0.0; vy[1:-1, :] = 0.0
+            o.set_start(np.concatenate([vx.ravel(), vy.ravel()]))
+        ia, ib = a.solve_increment(), b.solve_increment()
+        assert ia["iters"] == ib["iters"] and ia["iters"] >= 10
+        assert ib["frozen_at"] == 10 and ia["frozen_at"] == -1
+        assert ib["n_plastic"] == 0
+    for f in ("vx", "vy", "txx", "tyy", "txy", "p", "epl"):
+        assert np.array_equal(a.get(f), b.get(f)), f
+
+
+def test_frozen_plasticity_fixed_point_against_numpy():
+    """Sec. 3.3's frozen plasticity on a tiny plastic grid (Jaumann off,
+    elastic Maxwell limit): the converged state is the fixed point of the
+    pseudo-transient map with the scales s held, so at centres
+    tau = s (1 - bt) / (1 - bt s) tau_tr(v), at vertices the same with the
+    mean of the adjacent s, p = p_hat - K dt div v, and the momentum residual
+    of those stresses vanishes.  tau_tr, p and the residual are recomputed
+    here with numpy from the converged velocity; the held scales differ from
+    the yield condition's, which shows that the freeze acted."""
+    s, o = _plastic_tiny_2d(n_chk=10)
+    o.set_freeze(1, 0.0)
+    rates = [s.a, -s.a]
+    # an elastic first increment gives a history, the second one yields
+    o.apply_increment(rates, s.dt); o.solve_increment()
+    hist = {f: o.get(f) for f in ("txx", "tyy", "txy", "p")}
+    o.apply_increment(rates, s.dt)
+    info = o.solve_increment()
+    assert info["frozen_at"] == 10 and info["n_plastic"] > 0
+    bt, bp, vs = o.pt_params()
+    nx, ny = s.n
+    dx, dy = s.L[0] / nx, s.L[1] / ny
+    vx, vy = o.get("vx"), o.get("vy")            # (ny, nx+1), (ny+1, nx)
+    sc = o.get("scale")                          # (ny, nx)
+    dt, eta = s.dt, G * s.dt                     # eta_ve = G dt for mu_s = inf
+    exx = (vx[:, 1:] - vx[:, :-1]) / dx
+    eyy = (vy[1:, :] - vy[:-1, :]) / dy
+    div = exx + eyy
+    trxx = hist["txx"] + 2 * eta * (exx - div / 3)
+    tryy = hist["tyy"] + 2 * eta * (eyy - div / 3)
+    exy = np.zeros((ny + 1, nx + 1))
+    exy[1:-1, 1:-1] = 0.5 * ((vx[1:, 1:-1] - vx[:-1, 1:-1]) / dy + (vy[1:-1, 1:] - vy[1:-1, :-1]) / dx)
+    trxy = hist["txy"] + 2 * eta * exy
+    f = sc * (1 - bt) / (1 - bt * sc)
+    sv = np.zeros((ny + 1, nx + 1))
+    sv[1:-1, 1:-1] = 0.25 * (sc[1:, 1:] + sc[1:, :-1] + sc[:-1, 1:] + sc[:-1, :-1])
+    fv = sv * (1 - bt) / (1 - bt * sv)
+    txx, tyy, txy, p = o.get("txx"), o.get("tyy"), o.get("txy"), o.get("p")
+    scale = max(np.abs(txx).max(), np.abs(txy).max())
+    np.testing.assert_allclose(txx, f * trxx, rtol=0, atol=1e-11 * scale)
+    np.testing.assert_allclose(tyy, f * tryy, rtol=0, atol=1e-11 * scale)
+    np.testing.assert_allclose(txy[1:-1, 1:-1], (fv * trxy)[1:-1, 1:-1], rtol=0, atol=1e-11 * scale)
+    np.testing.assert_allclose(p, hist["p"] - K * dt * div, rtol=0, atol=1e-11 * scale)
+    Rx = ((txx - p)[:, 1:] - (txx - p)[:, :-1]) / dx + (txy[1:, 1:-1] - txy[:-1, 1:-1]) / dy
+    Ry = ((tyy - p)[1:, :] - (tyy - p)[:-1, :]) / dy + (txy[1:-1, 1:] - txy[1:-1, :-1]) / dx
+    assert max(np.abs(Rx).max(), np.abs(Ry).max()) * dx / scale < 1e-10
+    # the held scales are not those of the converged trial: the freeze acted
+    Tc = (1 - bt) / (1 - bt * sc)
+    Txx, Tyy = Tc * trxx, Tc * tryy
+    Tv = fv / np.where(sv > 0, sv, 1) * trxy
+    Txy_c = 0.25 * (Tv[1:, 1:] + Tv[1:, :-1] + Tv[:-1, 1:] + Tv[:-1, :-1])
+    sj = np.sqrt(0.5 * (Txx ** 2 + Tyy ** 2) + Txy_c ** 2)
+    Y = np.maximum(A2 * p + B2 * s.cohesion(), 0.0)
+    s_yield = np.where(sj > Y, Y / sj, 1.0)
+    assert np.abs(s_yield - sc).max() > 1e-6
