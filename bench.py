@@ -56,7 +56,9 @@ def parse():
     ap.add_argument("--warm-steps", type=int, default=150, help="training steps")
     ap.add_argument("--warm-base", type=int, default=32, help="base channels of the network")
     ap.add_argument("--batch", type=int, default=0, help="time the batched 2D solve of this many instances")
-    ap.add_argument("--batch-increment", type=int, default=2, help="batched increment that is timed")
+    ap.add_argument("--batch-increment", type=int, default=3, help="batched increment that is timed")
+    ap.add_argument("--batch-freeze", type=int, default=1,
+                    help="frozen plasticity after 16 n_x iterations in every instance (Sec. 3.3)")
     ap.add_argument("--batch-nchk", type=int, default=1000,
                     help="check interval of the batched FP32 solve (the FP32 stopping test needs long intervals)")
     ap.add_argument("--tol", type=float, default=1e-6)
@@ -465,7 +467,8 @@ def batch_arm(args):
     for s in setups:
         g = P.Grid(2, s.n, precision=P.FP32_MIXED, stream=stream.cuda_stream)
         g.set_material(s.K, s.G, s.mu_s, s.phi_deg, s.psi_deg, s.cohesion())
-        g.set_solver(tol=s.tol, max_iter=2000000, n_chk=args.batch_nchk)
+        g.set_solver(tol=s.tol, max_iter=2000000, n_chk=args.batch_nchk,
+                     freeze_iter=16 * s.n[0] if args.batch_freeze else 0)
         grids.append(g)
     B = P.Batch(grids)
     a, dt = setups[0].a, setups[0].dt
@@ -518,6 +521,8 @@ def batch_arm(args):
         small = [q for q in setups if q.n[0] == min(x.n[0] for x in setups)][0]
         o = O.from_setup(small)
         o.set_solver(tol=small.tol, max_iter=2000000, n_chk=100)
+        if args.batch_freeze:
+            o.set_freeze(16 * small.n[0], 1e-4)
         for _ in range(args.batch_increment - 1):
             o.apply_increment([a, -a, 0.0], dt)
             o.solve_increment()
@@ -535,8 +540,10 @@ def batch_arm(args):
         "value": gbs, "unit": "GB/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": sec / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "2d-batch %d instances of {127,255,383,511}^2, increment %d, tol 1e-6, fp32 sweeps"
-                   % (len(setups), args.batch_increment),
+        "config": {"workload": "2d-batch %d instances of {127,255,383,511}^2, increment %d, tol 1e-6, fp32 sweeps, "
+                               "check every %d iterations%s" % (len(setups), args.batch_increment, args.batch_nchk,
+                                                                ", frozen plasticity after 16 n_x iterations"
+                                                                if args.batch_freeze else ""),
                    "cells": sum(cells), "tile": tile, "iterations_min_max": [min(iters), max(iters)],
                    "iterations_sum": sum(iters),
                    "l2": "inputs larger than L2 while most instances iterate (%.1f GB per iteration)"

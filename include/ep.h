@@ -85,6 +85,13 @@ typedef struct {
   double xi;            /* multiplier of Re_opt = 3 sqrt(10) pi / 2 (1)       */
   double r_pt;          /* K~/G~ of Eq. PT23 (r_opt = 1/2)                    */
   int jaumann;          /* rotate the old stress (Eq. j1), default 1          */
+  /* frozen plasticity (Sec. 3.3): at the first check with k >= freeze_iter
+   * and eps_rel > freeze_eps, the centre return scales are held for the rest
+   * of the increment (the iteration becomes linear).  freeze_iter < 0 (the
+   * default) follows the paper: 16 n_x for grids of more than 10^6 cells,
+   * never otherwise; 0 never freezes. */
+  long long freeze_iter;
+  double freeze_eps;    /* default 1e-4                                        */
 } ep_solver_opts;
 
 typedef struct {
@@ -101,6 +108,7 @@ typedef struct {
   double sxx_int_right; /* the same along the rightmost column                */
   double ms;            /* device wall time of the solve, milliseconds       */
   int status;           /* ep_status of the solve                             */
+  long long frozen_at;  /* iteration at which the scales froze, -1 if never   */
 } ep_solve_info;
 
 /* Device bytes a grid needs.  Pass a buffer of at least this size to

@@ -30,7 +30,8 @@ FIELD_ID = {n: i for i, n in enumerate(FIELDS)}
 
 class SolverOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_longlong), ("n_chk", C.c_int),
-                ("c_cfl", C.c_double), ("xi", C.c_double), ("r_pt", C.c_double), ("jaumann", C.c_int)]
+                ("c_cfl", C.c_double), ("xi", C.c_double), ("r_pt", C.c_double), ("jaumann", C.c_int),
+                ("freeze_iter", C.c_longlong), ("freeze_eps", C.c_double)]
 
 
 class SolveInfo(C.Structure):
@@ -38,7 +39,7 @@ class SolveInfo(C.Structure):
                 ("eps_tau", C.c_double), ("eps_p", C.c_double), ("eps_rel", C.c_double),
                 ("max_r", C.c_double), ("max_sigma", C.c_double), ("n_plastic", C.c_longlong),
                 ("sxx_int_centre", C.c_double), ("sxx_int_right", C.c_double), ("ms", C.c_double),
-                ("status", C.c_int)]
+                ("status", C.c_int), ("frozen_at", C.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -193,7 +194,11 @@ class Grid:
         check(self.h, self._L.ep_default_solver(self.ndim, C.byref(o)))
         return o
 
-    def set_solver(self, tol=1e-8, max_iter=10000000, n_chk=100, c_cfl=None, xi=1.0, r_pt=0.5, jaumann=True):
+    def set_solver(self, tol=1e-8, max_iter=10000000, n_chk=100, c_cfl=None, xi=1.0, r_pt=0.5, jaumann=True,
+                   freeze_iter=-1, freeze_eps=1e-4):
+        """freeze_iter: frozen plasticity (Sec. 3.3) from this iteration on
+        when eps_rel > freeze_eps; -1 the paper's rule (16 n_x above 10^6
+        cells), 0 never."""
         o = self.default_solver()
         o.tol = tol
         o.max_iter = int(max_iter)
@@ -202,6 +207,8 @@ class Grid:
         o.xi = xi
         o.r_pt = r_pt
         o.jaumann = int(bool(jaumann))
+        o.freeze_iter = int(freeze_iter)
+        o.freeze_eps = float(freeze_eps)
         check(self.h, self._L.ep_set_solver(self.h, C.byref(o)))
 
     def apply_increment(self, a, dt, load_plane=LOAD_XY, body_force=None, use_warm_start=False):

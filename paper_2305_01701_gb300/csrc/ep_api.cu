@@ -249,6 +249,12 @@ Scal make_scal(const ep_grid *h) {
   s.tol = h->opts.tol;
   s.n_chk = h->opts.n_chk;
   s.jaumann = h->opts.jaumann;
+  // frozen plasticity: the paper's rule (16 n_x on grids above 10^6 cells)
+  // unless the caller set freeze_iter
+  long long fi = h->opts.freeze_iter;
+  if (fi < 0) fi = (double)h->g.nx * h->g.ny * h->g.nz > 1e6 ? 16LL * h->g.nx : 0;
+  s.freeze_iter = fi;
+  s.freeze_eps = h->opts.freeze_eps;
   double dxm = std::min(h->g.dx, h->g.dy), Lm = std::max(h->L[0], h->L[1]);
   if (h->ndim == 3) { dxm = std::min(dxm, h->g.dz); Lm = std::max(Lm, h->L[2]); }
   s.dxmin = dxm;
@@ -528,6 +534,7 @@ ep_status solve(ep_grid *h, ep_solve_info *info) {
   if (r != EP_OK) return r;
   DevInfo init{};
   init.max_iter = h->opts.max_iter;
+  init.frozen_at = -1;
   *h->hinfo = init;
   CK(h, cudaMemcpyAsync(h->dinfo, h->hinfo, sizeof(DevInfo), cudaMemcpyHostToDevice, h->stream));
   CK(h, cudaEventRecord(h->ev0, h->stream));
@@ -570,6 +577,7 @@ ep_status solve(ep_grid *h, ep_solve_info *info) {
     info->sxx_int_centre = line[0]; info->sxx_int_right = line[1];
     info->ms = ms;
     info->status = st;
+    info->frozen_at = di.frozen_at;
   }
   if (st == EP_ERR_DIVERGED) return fail(h, st, "NaN in a residual norm");
   if (st == EP_ERR_TIMEOUT) return fail(h, st, "a bounded device wait gave up");
@@ -607,6 +615,8 @@ ep_status ep_default_solver(int ndim, ep_solver_opts *o) {
   o->xi = 1.0;
   o->r_pt = 0.5;
   o->jaumann = 1;
+  o->freeze_iter = -1;
+  o->freeze_eps = 1e-4;
   return EP_OK;
 }
 
@@ -701,9 +711,9 @@ ep_status ep_set_material(ep_handle h, double K, double G, double mu_s, double p
 ep_status ep_set_solver(ep_handle h, const ep_solver_opts *o) {
   if (!h || !o) return fail(h, EP_ERR_ARG, "ep_set_solver: null argument");
   if (!(o->tol >= 0.0) || o->n_chk < 2 || (o->n_chk & 1) || o->max_iter < 0 || o->max_iter % o->n_chk ||
-      !(o->c_cfl > 0.0) || !(o->xi > 0.0) || !(o->r_pt > 0.0))
+      !(o->c_cfl > 0.0) || !(o->xi > 0.0) || !(o->r_pt > 0.0) || !(o->freeze_eps >= 0.0))
     return fail(h, EP_ERR_ARG, "ep_set_solver: need tol >= 0, even n_chk >= 2, max_iter a multiple of n_chk, "
-                               "c_cfl, xi, r_pt > 0");
+                               "c_cfl, xi, r_pt > 0, freeze_eps >= 0");
   if (o->n_chk != h->opts.n_chk && h->chunk) {
     cudaGraphExecDestroy(h->chunk);
     h->chunk = nullptr;
@@ -1231,7 +1241,7 @@ ep_status batch_solve(ep_batch *b, ep_solve_info *infos) {
       f.iters = di.iters; f.eps_res = di.eps_res; f.eps_mom = di.eps_mom; f.eps_tau = di.eps_tau;
       f.eps_p = di.eps_p; f.eps_rel = di.eps_rel; f.max_r = di.max_r; f.max_sigma = di.max_sig;
       f.n_plastic = (long long)npl; f.sxx_int_centre = line[0]; f.sxx_int_right = line[1];
-      f.ms = ms; f.status = st;
+      f.ms = ms; f.status = st; f.frozen_at = di.frozen_at;
     }
   }
   if (worst != EP_OK) return bfail(b, worst, "some grids of the batch did not converge");

@@ -68,6 +68,7 @@ __global__ void __launch_bounds__(TX *TY) k_fused2d(const Inst2<T> *insts, const
     const int4 item = items[it];
     const Inst2<T> &I = insts[item.x];
     if (*(volatile const int *)&I.di->done != 0) continue;   // uniform per block
+    const bool frozen = I.di->frozen != 0;
     const Geo &g = I.g;
     const Scal *sc = I.sc;
     const int i0 = item.y * TX, j0 = item.z * TY;
@@ -147,10 +148,14 @@ __global__ void __launch_bounds__(TX *TY) k_fused2d(const Inst2<T> *insts, const
         T txy = qr * (S.txy[p] + S.txy[p + 1] + S.txy[p + W] + S.txy[p + W + 1]);
         T T0 = S.tc0[p], T1 = S.tc1[p];
         T J2 = txy * txy + (T)0.5 * T0 * T0 + (T)0.5 * T1 * T1;
-        T sj = sqrt(J2);
-        T Y = Acoef * pr + I.yc[e];
-        Y = Y > (T)0 ? Y : (T)0;
-        s = sj > Y ? Y / sj : (T)1;
+        if (frozen) {
+          s = I.s[e];   // frozen plasticity: the held scale (Sec. 3.3)
+        } else {
+          T sj = sqrt(J2);
+          T Y = Acoef * pr + I.yc[e];
+          Y = Y > (T)0 ? Y : (T)0;
+          s = sj > Y ? Y / sj : (T)1;
+        }
         T n0 = s * T0, n1 = s * T1;
         sx = n0 - pr;
         sy = n1 - pr;
@@ -158,7 +163,7 @@ __global__ void __launch_bounds__(TX *TY) k_fused2d(const Inst2<T> *insts, const
           I.sn[o][0][e] = n0;
           I.sn[o][1][e] = n1;
           I.sp[o][e] = pr;
-          I.s[e] = s;
+          if (!frozen) I.s[e] = s;
           if (check) {
             sig = maxn(sig, maxn(fabs((double)sx), fabs((double)sy)));
             dtau = maxn(dtau, maxn(fabs((double)n0 - (double)I.cn[0][e]), fabs((double)n1 - (double)I.cn[1][e])));
@@ -279,6 +284,8 @@ __global__ void k_init_batch(const Inst2<T> *insts, int n, long long max_iter) {
   DevInfo *di = insts[q].di;
   for (int r = 0; r < RED_COUNT; ++r) di->red[r] = 0ull;
   di->done = 0;
+  di->frozen = 0;
+  di->frozen_at = -1;
   di->k_check = 0;
   di->max_iter = max_iter;
   di->iters = 0;

@@ -61,6 +61,7 @@ struct F3 {
   const T *tbn[3], *tbs[3], *pb, *yc;
   const T *rq[3], *rd[2];
   T *uo[3];
+  const T *s;   // centre return scales (read when plasticity is frozen)
 };
 
 // Load plane `lev` of the neighbour-read inputs into their ring slots.
@@ -96,6 +97,7 @@ template <typename T, int TY>
 __global__ void __launch_bounds__(TX * TY, 2) k_fused3d(Geo g, F3<T> A, const Scal *sc, const DevInfo *di, int kz) {
   constexpr int W = Smem<T, TY>::W, H = Smem<T, TY>::H, WH = Smem<T, TY>::WH, NT = TX * TY;
   if (di != nullptr && *(volatile const int *)&di->done != 0) return;
+  const bool frozen = di != nullptr && di->frozen;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem<T, TY> &S = *reinterpret_cast<Smem<T, TY> *>(smem_raw);
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
@@ -247,10 +249,14 @@ __global__ void __launch_bounds__(TX * TY, 2) k_fused3d(Geo g, F3<T> A, const Sc
         T tyz = qr * (S.tyz[om1][p] + S.tyz[om1][p + W] + S.tyz[o0][p] + S.tyz[o0][p + W]);
         T T0 = S.tc[0][p], T1 = S.tc[1][p], T2 = S.tc[2][p];
         T J2 = txy * txy + txz * txz + tyz * tyz + (T)0.5 * T0 * T0 + (T)0.5 * T1 * T1 + (T)0.5 * T2 * T2;
-        T sj = sqrt(J2);
-        T Y = Acoef * pr + A.yc[ec];
-        Y = Y > (T)0 ? Y : (T)0;
-        s = sj > Y ? Y / sj : (T)1;
+        if (frozen) {
+          s = A.s[ec];
+        } else {
+          T sj = sqrt(J2);
+          T Y = Acoef * pr + A.yc[ec];
+          Y = Y > (T)0 ? Y : (T)0;
+          s = sj > Y ? Y / sj : (T)1;
+        }
         T n0 = s * T0, n1 = s * T1, n2 = s * T2;
         sx = n0 - pr; sy = n1 - pr; sz = n2 - pr;
         if (a >= 2 && a < W - 2 && b >= 2 && b < H - 2 && lc >= kb && lc < ke) {
@@ -339,6 +345,7 @@ void launch_fused3d(const Geo &g, const Stage<T> &S, const Scal *sc, const DevIn
     A.tbn[d] = S.tbn[d]; A.tbs[d] = S.tbs[d]; A.rq[d] = S.rq[d]; A.uo[d] = S.uo[d];
   }
   A.sop = S.sop; A.snp = S.snp; A.pb = S.pb; A.yc = S.yc; A.rd[0] = S.rd[0]; A.rd[1] = S.rd[1];
+  A.s = S.s;
   kz = fused3d_kz(g, TX, TY, kz, 2);
   dim3 grid((g.px + TX - 1) / TX, (g.py + TY - 1) / TY, (g.pz + kz - 1) / kz);
   k_fused3d<T, TY><<<grid, TX * TY, sizeof(Smem<T, TY>), st>>>(g, A, sc, di, kz);

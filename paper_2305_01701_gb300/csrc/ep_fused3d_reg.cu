@@ -53,12 +53,14 @@ struct Args {
   const T *u[3], *rq[3], *rd[2];
   const T *son[3], *sos[3], *sop, *tbn[3], *tbs[3], *pb, *yc;
   T *snn[3], *sns[3], *snp, *uo[3];
+  const T *s;   // centre return scales (read when plasticity is frozen)
 };
 
 template <typename T, int H>
 __global__ void __launch_bounds__(WX *H, 1)
     k_fused3d_reg(const Args<T> A, Geo g, const Scal *sc, const DevInfo *di, int kz) {
   if (di != nullptr && *(volatile const int *)&di->done != 0) return;
+  const bool frozen = di != nullptr && di->frozen;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SmemR<T, H> &S = *reinterpret_cast<SmemR<T, H> *>(smem_raw);
   constexpr int W = WX;
@@ -242,10 +244,14 @@ __global__ void __launch_bounds__(WX *H, 1)
         const T txz = qr * (tsxz_1 + tsxz_1_xp + tsxz + tsxz_xp);
         const T tyz = qr * (tsyz_1 + tsyz_1_yp + tsyz + tsyz_yp);
         const T J2 = txy * txy + txz * txz + tyz * tyz + hf * c0v * c0v + hf * c1v * c1v + hf * c2v * c2v;
-        const T sj = sqrt(J2);
-        T Y = Acoef * pr + yc;
-        Y = Y > (T)0 ? Y : (T)0;
-        s_1 = sj > Y ? Y / sj : (T)1;
+        if (frozen) {
+          s_1 = A.s[(long long)lc * plane + col];
+        } else {
+          const T sj = sqrt(J2);
+          T Y = Acoef * pr + yc;
+          Y = Y > (T)0 ? Y : (T)0;
+          s_1 = sj > Y ? Y / sj : (T)1;
+        }
         const T n0 = s_1 * c0v, n1 = s_1 * c1v, n2 = s_1 * c2v;
         sxx_1 = n0 - pr; syy_1 = n1 - pr; szz_1 = n2 - pr;
         if (out_col && lc >= kb && lc < ke) {
@@ -334,6 +340,7 @@ void launch_fused3d_reg(const Geo &g, const Stage<T> &S, const Scal *sc, const D
   }
   A.rd[0] = S.rd[0]; A.rd[1] = S.rd[1];
   A.sop = S.sop; A.pb = S.pb; A.yc = S.yc; A.snp = S.snp;
+  A.s = S.s;
   kz = fused3d_kz(g, OX, H - 4, kz);
   dim3 grid((g.px + OX - 1) / OX, (g.py + H - 5) / (H - 4), (g.pz + kz - 1) / kz);
   k_fused3d_reg<T, H><<<grid, WX * H, sizeof(SmemR<T, H>), st>>>(A, g, sc, di, kz);

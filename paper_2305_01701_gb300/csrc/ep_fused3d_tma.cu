@@ -110,6 +110,7 @@ __device__ __forceinline__ void issue_plane(SmemT<T, TY> &S, const Maps &M, int 
 template <typename T>
 struct Out3 {
   T *snn[3], *sns[3], *snp, *uo[3];
+  const T *s;   // centre return scales (read when plasticity is frozen)
 };
 
 template <typename T, int TY>
@@ -118,6 +119,7 @@ __global__ void __launch_bounds__(TX *TY, 1)
   using L = Lay<T, TY>;
   constexpr int BW = L::BW, W = L::W, H = L::H, WH = L::WH, NT = TX * TY;
   if (di != nullptr && *(volatile const int *)&di->done != 0) return;
+  const bool frozen = di != nullptr && di->frozen;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   SmemT<T, TY> &S = *reinterpret_cast<SmemT<T, TY> *>(smem_raw);
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
@@ -280,10 +282,14 @@ __global__ void __launch_bounds__(TX *TY, 1)
         T tyz = qr * (S.tyz[om1][q] + S.tyz[om1][q + BW] + S.tyz[o0][q] + S.tyz[o0][q + BW]);
         T T0 = S.tc[0][q], T1 = S.tc[1][q], T2 = S.tc[2][q];
         T J2 = txy * txy + txz * txz + tyz * tyz + hf * T0 * T0 + hf * T1 * T1 + hf * T2 * T2;
-        T sj = sqrt(J2);
-        T Y = Acoef * pr + ycp[q];
-        Y = Y > (T)0 ? Y : (T)0;
-        s = sj > Y ? Y / sj : (T)1;
+        if (frozen) {
+          s = O.s[((long long)lc * g.py + gj) * px + gi];
+        } else {
+          T sj = sqrt(J2);
+          T Y = Acoef * pr + ycp[q];
+          Y = Y > (T)0 ? Y : (T)0;
+          s = sj > Y ? Y / sj : (T)1;
+        }
         T n0 = s * T0, n1 = s * T1, n2 = s * T2;
         sx = n0 - pr; sy = n1 - pr; sz = n2 - pr;
         if (a >= 2 && a < W - 2 && b >= 2 && b < H - 2 && lc >= kb && lc < ke) {
@@ -402,6 +408,7 @@ bool launch_fused3d_tma(const Geo &g, const Stage<T> &S, const Scal *sc, const D
   Out3<T> O;
   for (int d = 0; d < 3; ++d) { O.snn[d] = S.snn[d]; O.sns[d] = S.sns[d]; O.uo[d] = S.uo[d]; }
   O.snp = S.snp;
+  O.s = S.s;
   kz = fused3d_kz(g, TX, TY, kz);
   dim3 grid((g.px + TX - 1) / TX, (g.py + TY - 1) / TY, (g.pz + kz - 1) / kz);
   k_fused3d_tma<T, TY><<<grid, TX * TY, sizeof(SmemT<T, TY>), st>>>(M, O, g, sc, const_cast<DevInfo *>(di), kz);

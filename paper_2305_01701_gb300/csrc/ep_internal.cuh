@@ -42,6 +42,8 @@ struct Scal {
   double rate[3];
   long long n_chk;
   int jaumann;
+  long long freeze_iter;   // > 0: frozen plasticity armed from this iteration on
+  double freeze_eps;
 };
 
 // Reduction slots: bit patterns of non-negative doubles reduced with an
@@ -52,11 +54,12 @@ enum { RED_R = 0, RED_SIG, RED_DTAU, RED_DP, RED_DU, RED_V, RED_COUNT = 8 };
 struct DevInfo {
   unsigned long long red[RED_COUNT];
   int done;            // 0 running, 1 converged, 2 diverged, 3 reached max_iter
-  int pad;
+  int frozen;          // 1: the centre return scales are held (Sec. 3.3)
   long long k_check;   // iteration index of the next residual check
   long long max_iter;
   long long iters;     // index of the last check taken
   double eps_res, eps_mom, eps_tau, eps_p, eps_rel, max_r, max_sig;
+  long long frozen_at; // check at which the scales froze, -1 if not
 };
 
 // Pointers of one stage evaluation.  The same kernels serve the FP64
@@ -124,7 +127,14 @@ __device__ __forceinline__ void check_one(DevInfo *di, const Scal *sc) {
   if (isnan(er) || isnan(mr) || isnan(du)) di->done = 2;
   else if (er <= sc->tol) di->done = 1;
   else if (k >= di->max_iter) di->done = 3;
-  else di->k_check = k + sc->n_chk;
+  else {
+    di->k_check = k + sc->n_chk;
+    // frozen plasticity (Sec. 3.3): hold the scales of this check iteration
+    if (!di->frozen && sc->freeze_iter > 0 && k >= sc->freeze_iter && di->eps_rel > sc->freeze_eps) {
+      di->frozen = 1;
+      di->frozen_at = k;
+    }
+  }
   for (int r = 0; r < RED_COUNT; ++r) di->red[r] = 0ull;
 }
 

@@ -219,6 +219,7 @@ __global__ void __launch_bounds__(kThreads) k_return_centres(Geo g, Stage<T> S, 
   const int i = q.i, j = q.j, k = q.k;
   const long long c = q.e, px = g.px, pl = g.plane;
   const bool act = q.in && i < g.nx && j < g.ny && (ND == 2 || k < g.nz);
+  const bool frozen = di != nullptr && di->frozen;
   double sig = 0.0, dtau = 0.0, dp = 0.0;
   if (act) {
     const T qr = (T)0.25;
@@ -240,11 +241,16 @@ __global__ void __launch_bounds__(kThreads) k_return_centres(Geo g, Stage<T> S, 
       tn[d] = S.Tn[d][c];
       J2 += (T)0.5 * tn[d] * tn[d];
     }
-    T sj = sqrt(J2);
-    T Y = (T)sc->A * p + S.yc[c];
-    Y = Y > (T)0 ? Y : (T)0;
-    T s = sj > Y ? Y / sj : (T)1;
-    S.s[c] = s;
+    T s;
+    if (frozen) {
+      s = S.s[c];   // frozen plasticity: the held scale (Sec. 3.3)
+    } else {
+      T sj = sqrt(J2);
+      T Y = (T)sc->A * p + S.yc[c];
+      Y = Y > (T)0 ? Y : (T)0;
+      s = sj > Y ? Y / sj : (T)1;
+      S.s[c] = s;
+    }
     S.snp[c] = p;
 #pragma unroll
     for (int d = 0; d < ND; ++d) {

@@ -434,3 +434,53 @@ def test_batch_autotune_picks_a_tile_and_keeps_results(P):
         infos, st = batch.solve_increment()
         assert st == 0
     batch.close()
+
+
+def run_frozen_pair(P, s, increments, variant=None, kz=0, freeze_iter=100, batch=False):
+    """GPU FP64 against the oracle with frozen plasticity (Sec. 3.3) forced
+    early: same iterations, same freeze check, fields within 1e-10."""
+    g = gpu_grid(P, s, P.FP64, freeze_iter=freeze_iter, freeze_eps=0.0)
+    if variant is not None:
+        g.set_kernel(variant, kz)
+    o = O.from_setup(s)
+    o.set_freeze(freeze_iter, 0.0)
+    B = P.Batch([g]) if batch else None
+    fields = FIELDS_2D if s.ndim == 2 else FIELDS_3D
+    froze = 0
+    for inc in range(1, increments + 1):
+        if batch:
+            B.apply_increment(s.a, s.dt)
+            ig = B.solve_increment()[0][0]
+        else:
+            g.apply_increment_rates(rates_of(s), s.dt)
+            ig = g.solve_increment()
+        o.apply_increment(rates_of(s), s.dt)
+        io = o.solve_increment()
+        assert ig["iters"] == io["iters"], (inc, ig["iters"], io["iters"])
+        assert ig["frozen_at"] == io["frozen_at"], (inc, ig["frozen_at"], io["frozen_at"])
+        assert ig["n_plastic"] == io["n_plastic"], inc
+        froze += io["frozen_at"] >= 0
+        sc = group_scales(o, fields)
+        for f in fields:
+            e = rel_err(g.get(f), o.get(f), sc[f])
+            assert e <= 1e-10, (inc, f, e)
+    if B is not None:
+        B.close()
+    g.close()
+    return froze
+
+
+def test_frozen_plasticity_fp64_parity_2d_staged(P):
+    s = E.config(1, n=(40, 36), tol=1e-9, inclusion_radius=0.12)
+    assert run_frozen_pair(P, s, 9, variant=P.KERNEL_STAGED) >= 1
+
+
+def test_frozen_plasticity_fp64_parity_2d_batched(P):
+    s = E.config(1, n=(40, 36), tol=1e-9, inclusion_radius=0.12)
+    assert run_frozen_pair(P, s, 9, batch=True) >= 1
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+def test_frozen_plasticity_fp64_parity_3d(P, variant):
+    s = E.config(3, n=(20, 17, 14), tol=1e-9, precision="fp64", inclusion_radius=0.2)
+    assert run_frozen_pair(P, s, 7, variant=variant, kz=5) >= 1
