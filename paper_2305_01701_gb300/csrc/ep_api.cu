@@ -469,7 +469,8 @@ ep_status capture_chunk(ep_grid *h) {
   if (f2) {
     ep_status r = prepare_solo2d<T>(h);
     if (r != EP_OK) return r;
-    blocks = std::min(persistent_blocks(h->tile, sizeof(T)), h->n_items);
+    blocks = std::min(persistent_blocks(h->tile, sizeof(T)),
+                      (h->n_items + fused2d_items_per_block(h->tile) - 1) / fused2d_items_per_block(h->tile));
   }
   CK(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
   for (int it = 0; f2 && it < h->opts.n_chk; ++it) {
@@ -1017,7 +1018,8 @@ ep_status ep_time_sweep(ep_handle h, int iters, double *ms_out, int n_out, int *
     ep_status r = h->prec == EP_FP64 ? prepare_solo2d<double>(h) : prepare_solo2d<float>(h);
     if (r != EP_OK) return r;
     const size_t el = h->prec == EP_FP64 ? 8 : 4;
-    const int blocks = std::min(persistent_blocks(h->tile, el), h->n_items);
+    const int blocks = std::min(persistent_blocks(h->tile, el), (h->n_items + fused2d_items_per_block(h->tile) - 1) /
+                                                                    fused2d_items_per_block(h->tile));
     for (int it = 0; it < iters; ++it) {
       CK(h, cudaEventRecord(ev[0], h->stream));
       if (el == 8)
@@ -1103,7 +1105,7 @@ ep_status ep_set_kernel(ep_handle h, int variant, int shape) {
     return fail(h, EP_ERR_ARG, "ep_set_kernel: unknown variant");
   if ((variant == EP_KERNEL_FUSED_TMA || variant == EP_KERNEL_FUSED_REG) && h->ndim != 3)
     return fail(h, EP_ERR_ARG, "ep_set_kernel: the TMA and register sweeps are 3D only");
-  if (shape >= 0 && h->ndim == 2 && shape > 2)
+  if (shape >= 0 && h->ndim == 2 && shape >= FUSED2D_TILES)
     return fail(h, EP_ERR_ARG, "ep_set_kernel: shape is z-planes (3D, 0: by grid size) or a tile 0..2 (2D)");
   if (h->chunk) {
     cudaGraphExecDestroy(h->chunk);
@@ -1172,7 +1174,8 @@ ep_status batch_upload(ep_batch *b) {
   BCK(b, cudaMemcpy(b->insts, I.data(), I.size() * sizeof(Inst2<T>), cudaMemcpyHostToDevice));
   BCK(b, cudaMemcpy(b->items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
   b->n_items = (int)items.size();
-  b->blocks = std::min(persistent_blocks(b->tile, sizeof(T)), b->n_items);
+  b->blocks = std::min(persistent_blocks(b->tile, sizeof(T)),
+                       (b->n_items + fused2d_items_per_block(b->tile) - 1) / fused2d_items_per_block(b->tile));
   if (b->chunk) { cudaGraphExecDestroy(b->chunk); b->chunk = nullptr; }
   return EP_OK;
 }
@@ -1309,7 +1312,7 @@ ep_status ep_batch_solve_increment(ep_batch_handle b, ep_solve_info *infos) {
 }
 
 ep_status ep_batch_set_tile(ep_batch_handle b, int tile) {
-  if (!b || tile < 0 || tile > 2) return bfail(b, EP_ERR_ARG, "ep_batch_set_tile: tile must be 0..2");
+  if (!b || tile < 0 || tile >= FUSED2D_TILES) return bfail(b, EP_ERR_ARG, "ep_batch_set_tile: tile must be 0..4");
   b->tile = tile;
   return b->prec == EP_FP64 ? batch_upload<double>(b) : batch_upload<float>(b);
 }
@@ -1323,7 +1326,7 @@ ep_status ep_batch_autotune(ep_batch_handle b, int iters, int *tile_out) {
   BCK(b, cudaEventCreate(&e1));
   float best = 1e30f;
   int best_tile = 0;
-  for (int tile = 0; tile < 3; ++tile) {
+  for (int tile = 0; tile < FUSED2D_TILES; ++tile) {
     b->tile = tile;
     ep_status r = b->prec == EP_FP64 ? batch_upload<double>(b) : batch_upload<float>(b);
     if (r != EP_OK) return r;

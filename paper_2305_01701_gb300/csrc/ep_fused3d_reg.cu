@@ -183,7 +183,8 @@ __global__ void __launch_bounds__(WX *H, 1)
       const T pxz_1_xp = xp(pxz_1), pxz_xp = xp(pxz);
       const T pyz_1_yp = S.pyz[sl1].r[rb + 1][a], pyz_yp = S.pyz[sl].r[rb + 1][a];
 
-      if (a >= 1 && b < H - 1 && t >= 1 && t <= nz - 1 && gi >= 1 && gi <= nx - 1 && gj >= 0 && gj < ny) {
+      if (b < H - 1 && t >= 1 && t <= nz - 1)
+      if (a >= 1 && gi >= 1 && gi <= nx - 1 && gj >= 0 && gj < ny) {
         const T dzx = qr * (rd1_1_xm + rd1_1 + rd1_xm + rd1);
         const T Tyz = qr * (rq2_xm + rq2 + rq2_yp_xm + rq2_yp);
         const T Wyz = qr * (oyz_xm + oyz + oyz_yp_xm + oyz_yp);
@@ -192,7 +193,8 @@ __global__ void __launch_bounds__(WX *H, 1)
         const T tr = tbxz + two_eta * exz + (oxz * dzx + Tyz * Wxy - Txy * Wyz);
         tsxz = bt * soxz + ob * tr;
       }
-      if (a < W - 1 && b >= 1 && t >= 1 && t <= nz - 1 && gi >= 0 && gi < nx && gj >= 1 && gj <= ny - 1) {
+      if (b >= 1 && t >= 1 && t <= nz - 1)
+      if (a < W - 1 && gi >= 0 && gi < nx && gj >= 1 && gj <= ny - 1) {
         const T dzy = qr * ((rd1_1_ym - rd0_1_ym) + (rd1_1 - rd0_1) + (rd1_ym - rd0_ym) + (rd1 - rd0));
         const T Txy = qr * (rq0_1 + rq0_1_xp + rq0 + rq0_xp);
         const T Wxy = qr * (oxy_1 + oxy_1_xp + oxy + oxy_xp);
@@ -201,7 +203,8 @@ __global__ void __launch_bounds__(WX *H, 1)
         const T tr = tbyz + two_eta * eyz + (oyz * dzy - Txy * Wxz - Txz * Wxy);
         tsyz = bt * soyz + ob * tr;
       }
-      if (a >= 1 && b >= 1 && lc >= 0 && lc < nz && gi >= 1 && gi <= nx - 1 && gj >= 1 && gj <= ny - 1) {
+      if (b >= 1 && lc >= 0 && lc < nz)
+      if (a >= 1 && gi >= 1 && gi <= nx - 1 && gj >= 1 && gj <= ny - 1) {
         const T dyx = qr * (rd0_1_ym_xm + rd0_1_ym + rd0_1_xm + rd0_1);
         const T Tyz = qr * (rq2_1_xm + rq2_1 + rq2_xm + rq2);
         const T Wyz = qr * (oyz_1_xm + oyz_1 + oyz_xm + oyz);
@@ -210,7 +213,8 @@ __global__ void __launch_bounds__(WX *H, 1)
         const T tr = tbxy + two_eta * exy_1 + (oxy_1 * dyx + Tyz * Wxz + Txz * Wyz);
         tsxy = bt * soxy + ob * tr;
       }
-      if (a < W - 1 && b < H - 1 && lc >= 0 && lc < nz && gi >= 0 && gi < nx && gj >= 0 && gj < ny) {
+      if (b < H - 1 && lc >= 0 && lc < nz)
+      if (a < W - 1 && gi >= 0 && gi < nx && gj >= 0 && gj < ny) {
         exx = (u0_1_xp - u0_1) * rdx;
         eyy = (u1_1_yp - u1_1) * rdy;
         ezz = (u2 - u2_1) * rdz;
@@ -236,8 +240,8 @@ __global__ void __launch_bounds__(WX *H, 1)
       const T tsxy_yp_xp = xp(tsxy_yp);
       const T tsxz_1_xp = xp(tsxz_1), tsxz_xp = xp(tsxz);
       const T tsyz_1_yp = S.tsyz[sl1].r[rb + 1][a], tsyz_yp = S.tsyz[sl].r[rb + 1][a];
-      if (a >= 1 && a < W - 1 && b >= 1 && b < H - 1 && lc >= 0 && lc < nz && gi >= 0 && gi < nx && gj >= 0 &&
-          gj < ny) {
+      if (b >= 1 && b < H - 1 && lc >= 0 && lc < nz)
+      if (a >= 1 && a < W - 1 && gi >= 0 && gi < nx && gj >= 0 && gj < ny) {
         const T div = exx + eyy + ezz;
         const T pr = bp * sop + obp * (pb - KDt * div);
         const T txy = qr * (tsxy + tsxy_xp + tsxy_yp + tsxy_yp_xp);
@@ -247,10 +251,16 @@ __global__ void __launch_bounds__(WX *H, 1)
         if (frozen) {
           s_1 = A.s[(long long)lc * plane + col];
         } else {
-          const T sj = sqrt(J2);
           T Y = Acoef * pr + yc;
           Y = Y > (T)0 ? Y : (T)0;
-          s_1 = sj > Y ? Y / sj : (T)1;
+          if (sizeof(T) == 4) {
+            // FP32: compare squares and scale with the reciprocal square root
+            // only where the return acts (most cells stay elastic)
+            s_1 = J2 > Y * Y ? (T)(Y * rsqrtf((float)J2)) : (T)1;
+          } else {
+            const T sj = sqrt(J2);
+            s_1 = sj > Y ? Y / sj : (T)1;
+          }
         }
         const T n0 = s_1 * c0v, n1 = s_1 * c1v, n2 = s_1 * c2v;
         sxx_1 = n0 - pr; syy_1 = n1 - pr; szz_1 = n2 - pr;

@@ -138,8 +138,16 @@ __device__ __forceinline__ void check_one(DevInfo *di, const Scal *sc) {
   for (int r = 0; r < RED_COUNT; ++r) di->red[r] = 0ull;
 }
 
-// ---- batched fused 2D sweep (ep_fused2d.cu) -------------------------------
-// tile: 0 = 32x8, 1 = 32x16, 2 = 64x8 cells
+// ---- batched fused 2D sweep (ep_fused2d.cu, ep_fused2d_strip.cu) ---------
+// tile: 0 = 32x8, 1 = 32x16, 2 = 64x8 cells (block tiles in shared memory);
+// 3, 4 = warp strips of 28 columns marching 64 / 256 rows
+constexpr int FUSED2D_TILES = 5;
+inline int fused2d_items_per_block(int tile) { return tile >= 3 ? 8 : 1; }
+template <typename T>
+void launch_fused2d_strip(int seg, const Inst2<T> *insts, const int4 *items, int n_items, int b, int check,
+                          int blocks, cudaStream_t st);
+template <typename T>
+int fused2d_strip_blocks_per_sm(int seg);
 template <typename T>
 void launch_fused2d(int tile, const Inst2<T> *insts, const int4 *items, int n_items, int b, int check, int blocks,
                     cudaStream_t st);

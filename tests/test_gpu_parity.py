@@ -354,10 +354,13 @@ def test_fused_fp32_matches_staged_fp32(P):
                 assert np.abs(out[k][f] - out[0][f]).max() / scale <= 2e-5, (k, f)
 
 
-@pytest.mark.parametrize("tile", [0, 1, 2])
-def test_fused2d_fp64_parity(P, tile):
-    """The fused 2D kernel (a batch of one), in FP64, against the oracle."""
-    s = E.config(1, n=(70, 37), tol=1e-10)
+@pytest.mark.parametrize("tile,n", [(0, (70, 37)), (1, (70, 37)), (2, (70, 37)), (3, (70, 37)), (3, (30, 150)),
+                                    (4, (70, 37))])
+def test_fused2d_fp64_parity(P, tile, n):
+    """The fused 2D kernels (a batch of one), in FP64, against the oracle:
+    block tiles (0-2) and warp strips (3, 4) over several strips, segments
+    and ragged edges."""
+    s = E.config(1, n=n, tol=1e-10)
     g = gpu_grid(P, s, P.FP64)
     g.set_kernel(P.KERNEL_FUSED, tile)
     o = O.from_setup(s)
@@ -371,6 +374,28 @@ def test_fused2d_fp64_parity(P, tile):
             assert rel_err(g.get(f), o.get(f), sc[f]) <= 1e-10, (inc, f)
 
 
+@pytest.mark.parametrize("tile", [3, 4])
+def test_fused2d_strips_match_tiles_on_tall_grids(P, tile):
+    """Warp strips over several segments (64 / 256 rows) against the block
+    tile kernel, both FP64 on the GPU: same iterations, fields within 1e-10."""
+    s = E.config(1, n=(60, 560), tol=1e-9, c0=6e-4, inclusion_radius=0.1)
+    g0 = gpu_grid(P, s, P.FP64)
+    g0.set_kernel(P.KERNEL_FUSED, 0)
+    g1 = gpu_grid(P, s, P.FP64)
+    g1.set_kernel(P.KERNEL_FUSED, tile)
+    plastic = 0
+    for inc in range(1, 3):
+        g0.apply_increment(1.0, s.dt, P.LOAD_XY)
+        g1.apply_increment(1.0, s.dt, P.LOAD_XY)
+        i0, i1 = g0.solve_increment(), g1.solve_increment()
+        assert i0["iters"] == i1["iters"], inc
+        plastic += i0["n_plastic"] > 0
+        for f in FIELDS_2D:
+            assert rel_err(g1.get(f), g0.get(f)) <= 1e-10, (inc, f)
+    assert plastic >= 1
+    g0.close(); g1.close()
+
+
 def _batch_setups():
     sizes = [(24, 24), (31, 17), (40, 40), (16, 33), (9, 50)]
     out = []
@@ -380,8 +405,9 @@ def _batch_setups():
     return out
 
 
+@pytest.mark.parametrize("tile", [0, 3])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_batch_matches_solo_bit_for_bit(P, prec):
+def test_batch_matches_solo_bit_for_bit(P, prec, tile):
     """Every grid advanced inside a batch equals its own solo solve exactly
     (same kernel arithmetic, same iteration count), for uneven sizes and
     materials; FP64 instances also match the oracle."""
@@ -391,13 +417,13 @@ def test_batch_matches_solo_bit_for_bit(P, prec):
     grids = []
     for s in setups:
         g = gpu_grid(P, s, pr, tol=tol, max_iter=400000)
-        g.set_kernel(P.KERNEL_FUSED, 0)
+        g.set_kernel(P.KERNEL_FUSED, tile)
         grids.append(g)
     batch = P.Batch(grids)
     solos = []
     for s in setups:
         g = gpu_grid(P, s, pr, tol=tol, max_iter=400000)
-        g.set_kernel(P.KERNEL_FUSED, 0)
+        g.set_kernel(P.KERNEL_FUSED, tile)
         solos.append(g)
     oracles = [O.from_setup(s, tol=tol) for s in setups] if prec == "fp64" else None
     for inc in range(1, 7):
@@ -430,18 +456,20 @@ def test_batch_autotune_picks_a_tile_and_keeps_results(P):
         batch.apply_increment(1.0, 1e-4)
         if inc == 5:
             tile = batch.autotune(5)
-            assert tile in (0, 1, 2)
+            assert tile in (0, 1, 2, 3, 4)
         infos, st = batch.solve_increment()
         assert st == 0
     batch.close()
 
 
-def run_frozen_pair(P, s, increments, variant=None, kz=0, freeze_iter=100, batch=False):
+def run_frozen_pair(P, s, increments, variant=None, kz=0, freeze_iter=100, batch=False, tile=None):
     """GPU FP64 against the oracle with frozen plasticity (Sec. 3.3) forced
     early: same iterations, same freeze check, fields within 1e-10."""
     g = gpu_grid(P, s, P.FP64, freeze_iter=freeze_iter, freeze_eps=0.0)
     if variant is not None:
         g.set_kernel(variant, kz)
+    if tile is not None:
+        g.set_kernel(P.KERNEL_FUSED, tile)
     o = O.from_setup(s)
     o.set_freeze(freeze_iter, 0.0)
     B = P.Batch([g]) if batch else None
@@ -475,9 +503,10 @@ def test_frozen_plasticity_fp64_parity_2d_staged(P):
     assert run_frozen_pair(P, s, 9, variant=P.KERNEL_STAGED) >= 1
 
 
-def test_frozen_plasticity_fp64_parity_2d_batched(P):
+@pytest.mark.parametrize("tile", [0, 3])
+def test_frozen_plasticity_fp64_parity_2d_batched(P, tile):
     s = E.config(1, n=(40, 36), tol=1e-9, inclusion_radius=0.12)
-    assert run_frozen_pair(P, s, 9, batch=True) >= 1
+    assert run_frozen_pair(P, s, 9, batch=True, tile=tile) >= 1
 
 
 @pytest.mark.parametrize("variant", [0, 1, 2, 3])
