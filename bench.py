@@ -223,11 +223,17 @@ def one_step(P, g, s):
     return g.solve_increment()
 
 
+def check_interval(size, precision):
+    """Check every 100 iterations, or every 1000 for FP32 boxes above 200^3:
+    the FP32 stopping measure needs the longer interval there."""
+    return 1000 if precision == "fp32" and size > 200 else 100
+
+
 def make_grid(P, s, precision, kernel="auto", stream=None):
     g = P.Grid(3, s.n, s.L, precision=P.FP64 if precision == "fp64" else P.FP32_MIXED, stream=stream)
     g.set_kernel(KERNEL[kernel], -1)
     g.set_material(s.K, s.G, s.mu_s, s.phi_deg, s.psi_deg, s.cohesion())
-    g.set_solver(tol=s.tol, max_iter=2000000, n_chk=100)
+    g.set_solver(tol=s.tol, max_iter=2000000, n_chk=check_interval(s.n[0], precision))
     return g
 
 
@@ -253,6 +259,12 @@ def timed_steps(torch, P, g, s, stream, steps, barrier):
     ev1.record(stream)
     barrier()
     return ev0.elapsed_time(ev1) * 1e-3, infos
+
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# dominant kernel from one ncu capture of the benchmark command, by kernel and
+# box size; the entry must be dropped when the kernel changes.
+NCU_TRAFFIC = {("k_fused3d_reg", 127): 268.0e6}
 
 
 def kernel_names(ktimes, kernel):
@@ -284,6 +296,7 @@ def our_arm(args):
     for _ in range(args.warmup):           # full passes of the timed step
         one_step(P, g, s)
     bpc = g.sweep_bytes_per_cell()
+    nchk = check_interval(s.n[0], args.precision)
     clk = Clocks(local)
     clk.start()
     sec, infos = timed_steps(torch, P, g, s, stream, args.steps, barrier)
@@ -360,7 +373,10 @@ def our_arm(args):
     roof = {"bound": "hbm", "kernel": kernels[0] if len(kernels) == 1 else "staged sweep (5 kernels)",
             "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
             "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6800 GB/s",
-            "traffic": None, "kernel_ms": {k: float(ktimes[q]) for q, k in enumerate(kernels)},
+            "traffic": NCU_TRAFFIC.get((kernels[dom], s.n[0])),
+            "traffic_source": "ncu --set full capture of one launch of this command (profiles/)"
+                              if (kernels[dom], s.n[0]) in NCU_TRAFFIC else None,
+            "kernel_ms": {k: float(ktimes[q]) for q, k in enumerate(kernels)},
             "dominant": kernels[dom], "iteration_ms": float(it_ms), "alg_bytes_per_cell": bpc}
     line = {
         "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
@@ -369,7 +385,8 @@ def our_arm(args):
         "config": {"workload": "3d-ep-xz-inclusion %d^3, increment %d, tol %g, %s sweeps, plain start"
                    % (s.n[0], args.increment, args.tol, args.precision),
                    "sweep_kernel": kernels[0] if len(kernels) == 1 else "staged",
-                   "cells": cells, "iterations_per_step": infos[-1]["iters"],
+                   "cells": cells, "iterations_per_step": infos[-1]["iters"], "check_every": nchk,
+                   "frozen_at": infos[-1].get("frozen_at", -1),
                    "l2": "inputs larger than L2 (%d sweep arrays of %.1f MB)" % (33, cells * 4 / 1e6),
                    "parallelism": "replicas" if world > 1 else "single"},
         "ms_per_increment": ms_per_step,
@@ -377,7 +394,7 @@ def our_arm(args):
         # per step: (iters / n_chk + 1) graph chunks (staged: 5 n_chk + 1
         # kernels; fused: one staged check iteration, the check and n_chk - 1
         # fused sweeps), plus about 20 start-of-increment and 7 commit kernels
-        "gpu_launches": int(sum((i["iters"] // 100 + 1) * (501 if len(kernels) == 5 else 105) + 27
+        "gpu_launches": int(sum((i["iters"] // nchk + 1) * (5 * nchk + 1 if len(kernels) == 5 else nchk + 5) + 27
                                 for i in infos)),
         "roofline": roof,
         "e2e": e2e,

@@ -297,7 +297,10 @@ class Batch:
     """Many 2D grids advanced by one persistent kernel per iteration.
 
     The grids stay owned by the caller (keep them alive while the batch is
-    used); they must be 2D and share precision and n_chk.
+    used); they must be 2D and share precision and n_chk.  Call close()
+    before closing the grids: a batch that is garbage-collected without it
+    keeps its small device records rather than risk being destroyed after
+    its grids.
     """
 
     def __init__(self, grids):
@@ -312,9 +315,6 @@ class Batch:
         if getattr(self, "h", None):
             self._L.ep_destroy_batch(self.h)
             self.h = None
-
-    def __del__(self):
-        self.close()
 
     def apply_increment(self, a, dt):
         rates = _f64(a if np.ndim(a) else [a] * len(self.grids))

@@ -420,12 +420,20 @@ def test_batch_matches_solo_bit_for_bit(P, prec, tile):
         g.set_kernel(P.KERNEL_FUSED, tile)
         grids.append(g)
     batch = P.Batch(grids)
+    batch.set_tile(tile)
     solos = []
     for s in setups:
         g = gpu_grid(P, s, pr, tol=tol, max_iter=400000)
         g.set_kernel(P.KERNEL_FUSED, tile)
         solos.append(g)
     oracles = [O.from_setup(s, tol=tol) for s in setups] if prec == "fp64" else None
+    try:
+        _batch_vs_solo(P, batch, grids, setups, solos, oracles)
+    finally:
+        batch.close()
+
+
+def _batch_vs_solo(P, batch, grids, setups, solos, oracles):
     for inc in range(1, 7):
         batch.apply_increment(1.0, 1e-4)
         infos, st = batch.solve_increment()
@@ -443,7 +451,6 @@ def test_batch_matches_solo_bit_for_bit(P, prec, tile):
                 sc = group_scales(o, FIELDS_2D)
                 for f in FIELDS_2D:
                     assert rel_err(g.get(f), o.get(f), sc[f]) <= 1e-10, (inc, q, f)
-    batch.close()
 
 
 def test_batch_autotune_picks_a_tile_and_keeps_results(P):
@@ -452,14 +459,16 @@ def test_batch_autotune_picks_a_tile_and_keeps_results(P):
     for g in grids:
         g.set_kernel(P.KERNEL_FUSED, 0)
     batch = P.Batch(grids)
-    for inc in range(1, 6):
-        batch.apply_increment(1.0, 1e-4)
-        if inc == 5:
-            tile = batch.autotune(5)
-            assert tile in (0, 1, 2, 3, 4)
-        infos, st = batch.solve_increment()
-        assert st == 0
-    batch.close()
+    try:
+        for inc in range(1, 6):
+            batch.apply_increment(1.0, 1e-4)
+            if inc == 5:
+                tile = batch.autotune(5)
+                assert tile in (0, 1, 2, 3, 4)
+            infos, st = batch.solve_increment()
+            assert st == 0
+    finally:
+        batch.close()
 
 
 def run_frozen_pair(P, s, increments, variant=None, kz=0, freeze_iter=100, batch=False, tile=None):
@@ -473,6 +482,18 @@ def run_frozen_pair(P, s, increments, variant=None, kz=0, freeze_iter=100, batch
     o = O.from_setup(s)
     o.set_freeze(freeze_iter, 0.0)
     B = P.Batch([g]) if batch else None
+    if B is not None and tile is not None:
+        B.set_tile(tile)
+    try:
+        return _frozen_loop(P, s, g, o, B, increments)
+    finally:
+        if B is not None:
+            B.close()
+        g.close()
+
+
+def _frozen_loop(P, s, g, o, B, increments):
+    batch = B is not None
     fields = FIELDS_2D if s.ndim == 2 else FIELDS_3D
     froze = 0
     for inc in range(1, increments + 1):
@@ -492,9 +513,6 @@ def run_frozen_pair(P, s, increments, variant=None, kz=0, freeze_iter=100, batch
         for f in fields:
             e = rel_err(g.get(f), o.get(f), sc[f])
             assert e <= 1e-10, (inc, f, e)
-    if B is not None:
-        B.close()
-    g.close()
     return froze
 
 
