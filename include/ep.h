@@ -201,6 +201,10 @@ ep_status ep_batch_solve_increment(ep_batch_handle b, ep_solve_info *infos);
  * fastest (written to *tile_out when non-null) and restart the increments */
 ep_status ep_batch_autotune(ep_batch_handle b, int iters, int *tile_out);
 ep_status ep_batch_set_tile(ep_batch_handle b, int tile);
+/* time `iters` sweeps of the current tile over every grid of the open
+ * increments (all grids active, no checks): *ms_per_sweep receives the mean
+ * device time of one sweep; the increments then start again */
+ep_status ep_batch_time_sweep(ep_batch_handle b, int iters, double *ms_per_sweep);
 ep_status ep_destroy_batch(ep_batch_handle b);
 
 /* Learned warm start.  A convolutional U-Net (hand-written CUDA forward,

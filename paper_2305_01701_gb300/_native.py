@@ -76,6 +76,7 @@ SIGNATURES = [
     ("ep_batch_solve_increment", _I, [_P, C.POINTER(SolveInfo)]),
     ("ep_batch_autotune", _I, [_P, _I, _IP]),
     ("ep_batch_set_tile", _I, [_P, _I]),
+    ("ep_batch_time_sweep", _I, [_P, _I, _DP]),
     ("ep_destroy_batch", _I, [_P]),
     ("ep_net_create", _I, [_I, _I, _I, _I, _I, C.c_ulonglong, _P, C.POINTER(_P)]),
     ("ep_net_param_count", _I, [_P, C.POINTER(C.c_longlong)]),
@@ -334,6 +335,12 @@ class Batch:
 
     def set_tile(self, tile):
         check(None, self._L.ep_batch_set_tile(self.h, int(tile)))
+
+    def time_sweep(self, iters=10):
+        """Mean ms of one batched sweep (every grid active) on the open increments."""
+        ms = C.c_double()
+        check(None, self._L.ep_batch_time_sweep(self.h, int(iters), C.byref(ms)))
+        return ms.value
 
 
 def _ncheck(n, st):

@@ -1355,6 +1355,36 @@ ep_status ep_batch_autotune(ep_batch_handle b, int iters, int *tile_out) {
   return b->prec == EP_FP64 ? batch_restart<double>(b) : batch_restart<float>(b);
 }
 
+ep_status ep_batch_time_sweep(ep_batch_handle b, int iters, double *ms_per_sweep) {
+  if (!b || iters < 1 || !ms_per_sweep) return bfail(b, EP_ERR_ARG, "ep_batch_time_sweep: bad arguments");
+  for (int q = 0; q < b->count; ++q)
+    if (!b->g[q]->in_increment) return bfail(b, EP_ERR_STATE, "ep_batch_time_sweep: apply an increment first");
+  ep_status r = b->prec == EP_FP64 ? batch_upload<double>(b) : batch_upload<float>(b);
+  if (r != EP_OK) return r;
+  cudaEvent_t e0, e1;
+  BCK(b, cudaEventCreate(&e0));
+  BCK(b, cudaEventCreate(&e1));
+  for (int it = 0; it <= iters; ++it) {   // one untimed sweep, then `iters` timed ones
+    if (it == 1) BCK(b, cudaEventRecord(e0, b->stream));
+    if (b->prec == EP_FP64)
+      launch_fused2d<double>(b->tile, (const Inst2<double> *)b->insts, b->items, b->n_items, it & 1, 0, b->blocks,
+                             b->stream);
+    else
+      launch_fused2d<float>(b->tile, (const Inst2<float> *)b->insts, b->items, b->n_items, it & 1, 0, b->blocks,
+                            b->stream);
+  }
+  BCK(b, cudaEventRecord(e1, b->stream));
+  BCK(b, cudaEventSynchronize(e1));
+  BCK(b, cudaGetLastError());
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms_per_sweep = (double)ms / iters;
+  // the timed sweeps advanced the iterates: start the increments again
+  return b->prec == EP_FP64 ? batch_restart<double>(b) : batch_restart<float>(b);
+}
+
 ep_status ep_destroy_batch(ep_batch_handle b) {
   if (!b) return EP_OK;
   if (b->stream) cudaStreamSynchronize(b->stream);
