@@ -248,6 +248,19 @@ def prepare(P, s, precision, increment, kernel="auto", stream=None):
     return g
 
 
+def aggregate(torch, dist, seconds, units, device):
+    """The slowest rank's time and the units (bytes) all ranks processed.
+    Ranks run replicas (each solves its own copy, no data-path collective);
+    this is the only communication besides barriers."""
+    if dist is None:
+        return seconds, units
+    tmax = torch.tensor([seconds], dtype=torch.float64, device=device)
+    tot = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+    return float(tmax.item()), float(tot.item())
+
+
 def timed_steps(torch, P, g, s, stream, steps, barrier):
     """Run `steps` steps between CUDA events on the library's stream (with a
     barrier and a device synchronisation on both sides); returns (device
@@ -301,13 +314,9 @@ def our_arm(args):
     clk.start()
     sec, infos = timed_steps(torch, P, g, s, stream, args.steps, barrier)
     clocks = clk.stop()
-    tmax = sec
-    if dist:
-        t = torch.tensor([sec], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tmax = float(t.item())
     iters = sum(i["iters"] for i in infos)
-    gbs = bpc * cells * iters * world / tmax / 1e9
+    tmax, total_bytes = aggregate(torch, dist, sec, bpc * cells * iters, "cuda")
+    gbs = total_bytes / tmax / 1e9
     ms_per_step = tmax / args.steps * 1e3
 
     # dominant sweep kernel: CUDA events on the library's stream around a
