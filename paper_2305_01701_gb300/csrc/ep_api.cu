@@ -1020,6 +1020,9 @@ ep_status ep_time_sweep(ep_handle h, int iters, double *ms_out, int n_out, int *
     const size_t el = h->prec == EP_FP64 ? 8 : 4;
     const int blocks = std::min(persistent_blocks(h->tile, el), (h->n_items + fused2d_items_per_block(h->tile) - 1) /
                                                                     fused2d_items_per_block(h->tile));
+    // clear the record of the last solve (a converged grid would be skipped)
+    if (el == 8) launch_init_batch<double>((const Inst2<double> *)h->inst_dev, 1, 0, h->stream);
+    else launch_init_batch<float>((const Inst2<float> *)h->inst_dev, 1, 0, h->stream);
     for (int it = 0; it < iters; ++it) {
       CK(h, cudaEventRecord(ev[0], h->stream));
       if (el == 8)
@@ -1330,6 +1333,9 @@ ep_status ep_batch_autotune(ep_batch_handle b, int iters, int *tile_out) {
     b->tile = tile;
     ep_status r = b->prec == EP_FP64 ? batch_upload<double>(b) : batch_upload<float>(b);
     if (r != EP_OK) return r;
+    // clear the records of the last solve (a converged grid would be skipped)
+    if (b->prec == EP_FP64) launch_init_batch<double>((const Inst2<double> *)b->insts, b->count, 0, b->stream);
+    else launch_init_batch<float>((const Inst2<float> *)b->insts, b->count, 0, b->stream);
     // one untimed sweep, then `iters` timed sweeps without checks
     for (int it = 0; it <= iters; ++it) {
       if (it == 1) BCK(b, cudaEventRecord(e0, b->stream));
@@ -1361,6 +1367,9 @@ ep_status ep_batch_time_sweep(ep_batch_handle b, int iters, double *ms_per_sweep
     if (!b->g[q]->in_increment) return bfail(b, EP_ERR_STATE, "ep_batch_time_sweep: apply an increment first");
   ep_status r = b->prec == EP_FP64 ? batch_upload<double>(b) : batch_upload<float>(b);
   if (r != EP_OK) return r;
+  // clear the records of the last solve (a converged grid would be skipped)
+  if (b->prec == EP_FP64) launch_init_batch<double>((const Inst2<double> *)b->insts, b->count, 0, b->stream);
+  else launch_init_batch<float>((const Inst2<float> *)b->insts, b->count, 0, b->stream);
   cudaEvent_t e0, e1;
   BCK(b, cudaEventCreate(&e0));
   BCK(b, cudaEventCreate(&e1));
