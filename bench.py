@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--batch-increment", type=int, default=3, help="batched increment that is timed")
     ap.add_argument("--batch-freeze", type=int, default=1,
                     help="frozen plasticity after 16 n_x iterations in every instance (Sec. 3.3)")
+    ap.add_argument("--batch-tile", type=int, default=-1, help="2D kernel tile (-1: autotune)")
     ap.add_argument("--batch-nchk", type=int, default=1000,
                     help="check interval of the batched FP32 solve (the FP32 stopping test needs long intervals)")
     ap.add_argument("--tol", type=float, default=1e-6)
@@ -511,7 +512,11 @@ def batch_arm(args):
         return B.solve_increment()[0]
 
     B.apply_increment(a, dt)
-    tile = B.autotune(20)                  # restarts the open increments
+    if args.batch_tile >= 0:
+        B.set_tile(args.batch_tile)
+        tile = args.batch_tile
+    else:
+        tile = B.autotune(20)              # restarts the open increments
     B.solve_increment()
     for _ in range(args.warmup):
         step()
