@@ -11,7 +11,7 @@
 //     t it forms the vertex quantities of row t, the centres of row t - 1,
 //     the vertex deviators of row t - 1 and the velocities of row t - 2;
 //   * x +- 1 neighbours are warp shuffles, y - 1 neighbours are registers
-//     carried from the previous row; inputs are loaded one row ahead;
+//     carried from the previous row; inputs are loaded two rows ahead;
 //   * check iterations reduce the residual norms per warp (one atomic per
 //     warp, item and norm).
 // Warps take items independently, so a block never waits for another warp.
@@ -73,29 +73,36 @@ __global__ void __launch_bounds__(SW *SWARPS) k_fused2d_strip(const Inst2<T> *in
     auto at = [&](int row) { return (long long)row * px + gi; };
     auto ld = [&](const T *p, int row) -> T { return (xin && row >= 0 && row < py) ? p[at(row)] : (T)0; };
 
-    // inputs of the next row: vertex / face arrays of row t, centre arrays of row t - 1
-    T n_vx, n_vy, n_rq, n_rd, n_tbs, n_ss, n_tbn0, n_tbn1, n_sn0, n_sn1, n_sp, n_pb, n_yc;
-    auto prefetch = [&](int t) {
-      n_vx = ld(u0, t); n_vy = ld(u1, t); n_rq = ld(I.rq, t); n_rd = ld(I.rd, t);
-      n_tbs = ld(I.tbs, t); n_ss = ld(I.ss[b], t);
-      const int c = t - 1;
-      n_tbn0 = ld(I.tbn[0], c); n_tbn1 = ld(I.tbn[1], c); n_sn0 = ld(I.sn[b][0], c); n_sn1 = ld(I.sn[b][1], c);
-      n_sp = ld(I.sp[b], c); n_pb = ld(I.pb, c); n_yc = ld(I.yc, c);
+    // inputs two rows ahead (vertex / face arrays of row r, centre arrays of
+    // row r - 1): `next` holds row t + 1, `after` row t + 2
+    struct Row {
+      T vx, vy, rq, rd, tbs, ss, tbn0, tbn1, sn0, sn1, sp, pb, yc;
     };
+    auto load_row = [&](int r, Row &w) {
+      w.vx = ld(u0, r); w.vy = ld(u1, r); w.rq = ld(I.rq, r); w.rd = ld(I.rd, r);
+      w.tbs = ld(I.tbs, r); w.ss = ld(I.ss[b], r);
+      const int c = r - 1;
+      w.tbn0 = ld(I.tbn[0], c); w.tbn1 = ld(I.tbn[1], c); w.sn0 = ld(I.sn[b][0], c); w.sn1 = ld(I.sn[b][1], c);
+      w.sp = ld(I.sp[b], c); w.pb = ld(I.pb, c); w.yc = ld(I.yc, c);
+    };
+    Row next, after;
 
     // row history (suffix _1: row t - 1, _2: row t - 2, _3: row t - 3)
     T vx = 0, vy = 0, vx_1 = 0, vy_1 = 0, vx_2 = 0, vy_2 = 0, rd = 0, rd_1 = 0;
     T P_1 = 0, ts_1 = 0, s_2 = 0, sxx_2 = 0, syy_2 = 0, syy_3 = 0, nxy_2 = 0;
     double sig = 0.0, dtau = 0.0, dp = 0.0, rmax = 0.0, du = 0.0, vm = 0.0;
 
-    prefetch(j0 - 2);
+    load_row(j0 - 2, next);
+    load_row(j0 - 1, after);
     for (int t = j0 - 2; t < j1 + 2; ++t) {
       const int c = t - 1, u = t - 2;
       vx_2 = vx_1; vy_2 = vy_1; vx_1 = vx; vy_1 = vy; rd_1 = rd;
-      vx = n_vx; vy = n_vy; rd = n_rd;
-      const T rq = n_rq, tbs = n_tbs, ssv = n_ss;
-      const T tbn0 = n_tbn0, tbn1 = n_tbn1, sn0 = n_sn0, sn1 = n_sn1, sp = n_sp, pb = n_pb, yc = n_yc;
-      if (t + 1 < j1 + 2) prefetch(t + 1);
+      vx = next.vx; vy = next.vy; rd = next.rd;
+      const T rq = next.rq, tbs = next.tbs, ssv = next.ss;
+      const T tbn0 = next.tbn0, tbn1 = next.tbn1, sn0 = next.sn0, sn1 = next.sn1, sp = next.sp, pb = next.pb,
+              yc = next.yc;
+      next = after;
+      if (t + 2 < j1 + 2) load_row(t + 2, after);
 
       // ---- vertex (gi, t): shear strain rate, spin, relaxed trial ----
       const T vy_xm = xm(vy), rd_xm = xm(rd), rd_1_xm = xm(rd_1);
