@@ -12,8 +12,8 @@ each step so that every step does the same work.  The same increment is
 then solved once with plain FP64 sweeps ("fp64_plain").
 
 --size 511 runs the 511^3 box of the same setup.  Its first plastic
-increment needs well over 10^4 iterations (hours in FP64), so it is not the
-default step.
+increment takes about 13,000 iterations with frozen plasticity (about 90 s in
+FP32 and 12 minutes in FP64), so it is not the default step.
 
 Metric: effective HBM throughput of the sweeps (algorithmic bytes per cell
 per iteration x cells x iterations / device time) and the wall time per
