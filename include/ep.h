@@ -176,7 +176,7 @@ ep_status ep_set_fields(ep_handle h, int field, const double *host_in, size_t co
  * kernels (0, the default: chosen from the grid size so that the launch
  * fills every SM); in 2D the tile of the fused kernel (0: 32x8, 1: 32x16,
  * 2: 64x8 cells in shared memory; 3, 4: one warp per strip of 28 columns
- * marching 64 / 256 rows with its row history in registers). */
+ * marching 64 / 32 rows with its row history in registers). */
 enum { EP_KERNEL_AUTO = -1, EP_KERNEL_STAGED = 0, EP_KERNEL_FUSED = 1, EP_KERNEL_FUSED_TMA = 2, EP_KERNEL_FUSED_REG = 3 };
 ep_status ep_set_kernel(ep_handle h, int variant, int shape);
 

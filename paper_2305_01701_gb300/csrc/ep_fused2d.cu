@@ -262,14 +262,14 @@ void launch_fused2d(int tile, const Inst2<T> *insts, const int4 *items, int n_it
     case 1: launch_fused2d_t<T, 32, 16>(insts, items, n_items, b, check, blocks, st); break;
     case 2: launch_fused2d_t<T, 64, 8>(insts, items, n_items, b, check, blocks, st); break;
     case 3: launch_fused2d_strip<T>(64, insts, items, n_items, b, check, blocks, st); break;
-    default: launch_fused2d_strip<T>(256, insts, items, n_items, b, check, blocks, st); break;
+    default: launch_fused2d_strip<T>(32, insts, items, n_items, b, check, blocks, st); break;
   }
 }
 
 void fused2d_tile(int tile, int *tx, int *ty) {
-  if (tile >= 3) {   // warp strips: 28 written columns, 64 or 256 rows
+  if (tile >= 3) {   // warp strips: 28 written columns, 64 or 32 rows
     *tx = 28;
-    *ty = tile == 3 ? 64 : 256;
+    *ty = tile == 3 ? 64 : 32;
     return;
   }
   *tx = tile == 2 ? 64 : 32;
@@ -312,7 +312,7 @@ void launch_check_batch(const Inst2<T> *insts, int n, cudaStream_t st) {
 
 template <typename T>
 int fused2d_blocks_per_sm(int tile) {
-  if (tile >= 3) return fused2d_strip_blocks_per_sm<T>(tile == 3 ? 64 : 256);
+  if (tile >= 3) return fused2d_strip_blocks_per_sm<T>(tile == 3 ? 64 : 32);
   int nb = 0;
   cudaError_t e;
   if (tile == 0)

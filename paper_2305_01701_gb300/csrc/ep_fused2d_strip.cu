@@ -5,7 +5,7 @@
 // Drucker-Prager return at centres, vertex deviators, momentum residual and
 // velocity update; Eqs. A41, A5, A23ssP, A2ssP, A61, A6121lambda, A22S,
 // A22P), mapped without shared memory or block barriers:
-//   * a work item is (instance, strip of 28 columns, segment of SEG rows);
+//   * a work item is (instance, strip of 28 columns, segment of `seg` rows);
 //     lane a owns column x = i0 - 2 + a (lanes 2..29 are written);
 //   * the warp marches the rows y = j0 - 2 .. j1 + 1 of its segment: at row
 //     t it forms the vertex quantities of row t, the centres of row t - 1,
@@ -46,9 +46,9 @@ __device__ __forceinline__ void warp_max(double v, unsigned long long *slot) {
   if ((threadIdx.x & 31) == 0 && x) atomicMax(slot, x);
 }
 
-template <typename T, int SEG>
+template <typename T>
 __global__ void __launch_bounds__(SW *SWARPS) k_fused2d_strip(const Inst2<T> *insts, const int4 *items, int n_items,
-                                                              int b, int check) {
+                                                              int b, int check, int seg) {
   const int a = threadIdx.x & 31;
   const int warps = gridDim.x * (blockDim.x >> 5);
   const int o = 1 - b;
@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(SW *SWARPS) k_fused2d_strip(const Inst2<T> *in
     const Scal *sc = I.sc;
     const int nx = g.nx, ny = g.ny, py = g.py;
     const long long px = g.px;
-    const int i0 = item.y * SO, j0 = item.z * SEG, j1 = min(j0 + SEG, py);
+    const int i0 = item.y * SO, j0 = item.z * seg, j1 = min(j0 + seg, py);
     const int gi = i0 - 2 + a;
     const bool xin = gi >= 0 && gi < g.px;
     const bool out_col = a >= 2 && a < SW - 2 && xin;
@@ -230,15 +230,14 @@ __global__ void __launch_bounds__(SW *SWARPS) k_fused2d_strip(const Inst2<T> *in
 template <typename T>
 void launch_fused2d_strip(int seg, const Inst2<T> *insts, const int4 *items, int n_items, int b, int check,
                           int blocks, cudaStream_t st) {
-  if (seg <= 64) k_fused2d_strip<T, 64><<<blocks, SW * SWARPS, 0, st>>>(insts, items, n_items, b, check);
-  else k_fused2d_strip<T, 256><<<blocks, SW * SWARPS, 0, st>>>(insts, items, n_items, b, check);
+  k_fused2d_strip<T><<<blocks, SW * SWARPS, 0, st>>>(insts, items, n_items, b, check, seg);
 }
 
 template <typename T>
 int fused2d_strip_blocks_per_sm(int seg) {
+  (void)seg;
   int nb = 0;
-  cudaError_t e = seg <= 64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fused2d_strip<T, 64>, SW * SWARPS, 0)
-                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fused2d_strip<T, 256>, SW * SWARPS, 0);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fused2d_strip<T>, SW * SWARPS, 0);
   return e == cudaSuccess && nb > 0 ? nb : 1;
 }
 

@@ -140,7 +140,7 @@ __device__ __forceinline__ void check_one(DevInfo *di, const Scal *sc) {
 
 // ---- batched fused 2D sweep (ep_fused2d.cu, ep_fused2d_strip.cu) ---------
 // tile: 0 = 32x8, 1 = 32x16, 2 = 64x8 cells (block tiles in shared memory);
-// 3, 4 = warp strips of 28 columns marching 64 / 256 rows
+// 3, 4 = warp strips of 28 columns marching 64 / 32 rows
 constexpr int FUSED2D_TILES = 5;
 inline int fused2d_items_per_block(int tile) { return tile >= 3 ? 8 : 1; }
 template <typename T>

@@ -376,7 +376,7 @@ def test_fused2d_fp64_parity(P, tile, n):
 
 @pytest.mark.parametrize("tile", [3, 4])
 def test_fused2d_strips_match_tiles_on_tall_grids(P, tile):
-    """Warp strips over several segments (64 / 256 rows) against the block
+    """Warp strips over several segments (64 / 32 rows) against the block
     tile kernel, both FP64 on the GPU: same iterations, fields within 1e-10."""
     s = E.config(1, n=(60, 560), tol=1e-9, c0=6e-4, inclusion_radius=0.1)
     g0 = gpu_grid(P, s, P.FP64)
