@@ -82,6 +82,10 @@ def run_pair(P, s, increments, precision=None, fields=None, tol_fields=1e-10, sa
         io = o.solve_increment()
         if same_iters:
             assert ig["iters"] == io["iters"], (inc, ig, io)
+        if tol_fields is not None:   # the line integrals of sigma_xx (G15)
+            iscale = max(np.abs(o.get("txx")).max(), np.abs(o.get("p")).max()) * max(s.L)
+            for k in ("sxx_int_centre", "sxx_int_right"):
+                assert abs(ig[k] - io[k]) <= tol_fields * max(abs(io[k]), iscale), (inc, k, ig[k], io[k])
         assert ig["n_plastic"] == io["n_plastic"] or not same_iters, (inc, ig["n_plastic"], io["n_plastic"])
         sc = group_scales(o, fields)
         for f in fields:

@@ -55,6 +55,9 @@ def test_p1_homogeneous_elastic_2d(n):
         x = -0.5 + np.arange(n[0] + 1) / n[0]
         np.testing.assert_allclose(o.get("vx"), np.broadcast_to(x, (n[1], n[0] + 1)), atol=1e-15)
         np.testing.assert_allclose(o.get("ux"), inc * dt * np.broadcast_to(x, (n[1], n[0] + 1)), atol=1e-15)
+        # the integrated sigma_xx over a vertical line (G15) is sigma_xx * L_y
+        assert info["sxx_int_centre"] == pytest.approx(2 * G * eps * 1.0, rel=1e-12)
+        assert info["sxx_int_right"] == pytest.approx(2 * G * eps * 1.0, rel=1e-12)
 
 
 def test_p1_zero_interior_start_converges_to_background():
