@@ -647,3 +647,51 @@ def test_frozen_plasticity_fixed_point_against_numpy():
     Y = np.maximum(A2 * p + B2 * s.cohesion(), 0.0)
     s_yield = np.where(sj > Y, Y / sj, 1.0)
     assert np.abs(s_yield - sc).max() > 1e-6
+
+
+# -------------------------------------------------------------- golden ------
+def _golden():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "closed_forms.txt")
+    out = {}
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        name, value, _ = line.split(" ", 2)
+        out[name] = float(value)
+    return out
+
+
+def test_golden_closed_forms_against_the_oracle():
+    """The oracle reproduces the values the paper's formulas fix
+    (tests/golden/closed_forms.txt): the Drucker-Prager plateaus of a
+    homogeneous box in 2D and 3D, the PT constants behind beta, and the first
+    plastic increment of the Maxwell recurrence."""
+    gd = _golden()
+    # 2D and 3D plateaus (A = 0 effect: p = 0 under pure shear)
+    o = _grid(2, (2, 2), 1.5e-3)
+    for _ in range(10):
+        o.apply_increment([1.0, -1.0], 1e-4); o.solve_increment()
+    sj = np.sqrt(0.5 * (o.get("txx") ** 2 + o.get("tyy") ** 2))
+    np.testing.assert_allclose(sj, gd["plateau_2d_c1.5e-3"], rtol=1e-12)
+    o = _grid(3, (2, 2, 2), 1.5e-3)
+    for _ in range(12):
+        o.apply_increment([1.0, 0.0, -1.0], 1e-4); o.solve_increment()
+    sj = np.sqrt(0.5 * sum(o.get(f) ** 2 for f in ("txx", "tyy", "tzz")))
+    np.testing.assert_allclose(sj, gd["plateau_3d_c1.5e-3"], rtol=1e-12)
+    # beta_tau from Re_opt and r_opt (Eqs. PT1-PT24qq) on a 64^2 box
+    o = _grid(2, (64, 64), 1.0)
+    o.apply_increment([1.0, -1.0], 1e-4)
+    bt, bp, vs = o.pt_params()
+    eta, Vp = G * 1e-4, 0.9 / math.sqrt(2) / 64
+    rho = gd["re_opt"] * eta / Vp
+    Gt = rho * Vp ** 2 / (gd["r_opt"] + 4 / 3)
+    assert bt == pytest.approx((1 / (2 * Gt)) / (1 / (2 * Gt) + 1 / (2 * eta)), rel=1e-13)
+    # the Maxwell recurrence first reaches the plateau at the printed increment
+    o = _grid(2, (2, 2), 1.5e-3, mu_s=1e-3)
+    first = None
+    for inc in range(1, 15):
+        o.apply_increment([1.0, -1.0], 1e-4); o.solve_increment()
+        if first is None and o.get("epl").max() > 0:
+            first = inc
+    assert first == int(gd["maxwell_first_plastic_increment"])
