@@ -440,9 +440,11 @@ def warm_arm(args, torch, P, stream, barrier, s, cells):
         W.collect(gt, ts.a, ts.dt, incs, data, load_plane=P.LOAD_XZ)
         gt.close()
         groups.append(data)
+    loss_before = W.evaluate(net, groups)
     losses = W.train(net, groups, steps=args.warm_steps, lr=1e-3, batch=2)
     torch.cuda.synchronize()
     t_train = _t.perf_counter() - t_train0
+    loss_after, loss_zero = W.evaluate(net, groups), W.zero_loss(groups)
 
     g = prepare(P, s, "fp32", args.warm_increment, args.kernel, stream.cuda_stream)
     g.attach_warm_start(net)
@@ -470,8 +472,9 @@ def warm_arm(args, torch, P, stream, barrier, s, cells):
            "warm_GB_per_s": bpc * cells * res[True][1]["iters"] / (res[True][0] * 1e-3) / 1e9,
            "net": "3-level U-Net, base %d, BF16 weights, FP32 accumulation" % args.warm_base,
            "training": {"setups": args.warm_train, "samples": sum(d.n for d in groups), "steps": args.warm_steps,
-                        "first_loss": float(losses[0]), "last_loss": float(sum(losses[-10:]) / 10),
-                        "seconds": t_train}}
+                        "train_mse_before": loss_before, "train_mse_after": loss_after,
+                        "train_mse_zero_net": loss_zero,
+                        "last_minibatch_loss": float(sum(losses[-10:]) / 10), "seconds": t_train}}
     g.close()
     net.close()
     return out

@@ -403,6 +403,13 @@ class Net:
                                                   g.ctypes.data_as(C.POINTER(C.c_float)), n))
         return loss.value, g
 
+    def loss(self, x_ptr, t_ptr, N, size):
+        """MSE of the network on N samples (ep_net_gradients without the
+        gradient copy)."""
+        out = C.c_double()
+        _ncheck(self.h, self._L.ep_net_gradients(self.h, x_ptr, t_ptr, N, self._size(size), C.byref(out), None, 0))
+        return out.value
+
     def train_step(self, x_ptr, t_ptr, N, size, lr):
         loss = C.c_double()
         _ncheck(self.h, self._L.ep_net_train_step(self.h, x_ptr, t_ptr, N, self._size(size), float(lr),

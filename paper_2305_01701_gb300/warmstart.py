@@ -8,7 +8,9 @@ c / max(c).  The target (computed after the solve) is this increment's
 velocity change over S minus the previous one.  So the network learns a
 correction to "repeat the last increment", and a zero network reproduces
 that extrapolation.  PyTorch only supplies the device buffers the library
-writes into; every arithmetic step runs in the library.
+writes into; every arithmetic step of collection, training and inference
+runs in the library (`zero_loss` reduces the stored targets with torch, for
+the report only).
 """
 from __future__ import annotations
 
@@ -73,3 +75,26 @@ def train(net, groups, steps=400, lr=1e-3, batch=8, seed=0):
         size = list(g.dims[:g.ndim])
         losses.append(net.train_step(g.ptr_x(i0), g.ptr_t(i0), nb, size, lr))
     return losses
+
+
+def evaluate(net, groups, batch=2):
+    """Mean MSE of the network over every stored sample (weighted by sample)."""
+    total, count = 0.0, 0
+    for g in groups:
+        size = list(g.dims[:g.ndim])
+        for i0 in range(0, g.n, batch):
+            nb = min(batch, g.n - i0)
+            total += net.loss(g.ptr_x(i0), g.ptr_t(i0), nb, size) * nb
+            count += nb
+    return total / max(count, 1)
+
+
+def zero_loss(groups):
+    """The same mean MSE for a network that outputs zero, i.e. for plain
+    extrapolation of the last increment (the warm start's fallback)."""
+    total, count = 0.0, 0
+    for g in groups:
+        if g.n:
+            total += float((g.t[:g.n].double() ** 2).mean()) * g.n
+            count += g.n
+    return total / max(count, 1)

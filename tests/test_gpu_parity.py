@@ -298,16 +298,17 @@ def test_torch_workspace_and_stream(P):
     del ws
 
 
-def run_pair_kernel(P, s, increments, variant, kz, precision=None, tol_fields=1e-10, **solver):
+def run_pair_kernel(P, s, increments, variant, kz, precision=None, tol_fields=1e-10, dt_scale=(1.0,), **solver):
     precision = P.FP64 if precision is None else precision
     g = gpu_grid(P, s, precision, **solver)
     g.set_kernel(variant, kz)
     o = O.from_setup(s, **solver)
     fields = FIELDS_3D
     for inc in range(1, increments + 1):
-        g.apply_increment_rates(rates_of(s), s.dt)
+        dt = s.dt * dt_scale[inc % len(dt_scale)]
+        g.apply_increment_rates(rates_of(s), dt)
         ig = g.solve_increment()
-        o.apply_increment(rates_of(s), s.dt)
+        o.apply_increment(rates_of(s), dt)
         io = o.solve_increment()
         assert ig["iters"] == io["iters"], (inc, ig["iters"], io["iters"])
         sc = group_scales(o, fields)
@@ -325,6 +326,16 @@ def test_fused_kernel_fp64_parity_3d(P, n, kz, variant):
     ragged y tiles and z-chunk boundaries."""
     s = E.config(3, n=n, tol=1e-9, precision="fp64", inclusion_radius=0.15)
     run_pair_kernel(P, s, 7, variant, kz)
+
+
+@pytest.mark.parametrize("variant", [1, 2, 3])
+def test_fused_kernel_fp64_parity_3d_changing_dt(P, variant):
+    """Maxwell medium (eta_ve, K dt and the PT weights all depend on dt) with
+    dt changing between increments: the captured chunk graph is reused
+    across increments, so every sweep must read the scalars of the current
+    increment."""
+    s = E.config(3, n=(19, 15, 12), tol=1e-9, precision="fp64", inclusion_radius=0.2, mu_s=2e-3)
+    run_pair_kernel(P, s, 6, variant, 5, dt_scale=(1.0, 0.5, 2.0))
 
 
 @pytest.mark.parametrize("variant", [1, 2, 3])

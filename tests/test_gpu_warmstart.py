@@ -61,6 +61,7 @@ def test_net_forward_and_gradient_match_oracle(P, nd, shape, base, levels):
     xr = x.astype(np.float32).astype(np.float64)
     tr = t.astype(np.float32).astype(np.float64)
     assert abs(loss - U.loss(pk, xr, tr, nd, cin, cout, base, levels)) <= 1e-4 * loss
+    assert net.loss(xg.data_ptr(), tg.data_ptr(), N, list(shape)) == loss   # the same pass, no gradient copy
     g_ref = U.fd_gradient(pk, xr, tr, nd, cin, cout, base, levels, h=1e-5)
     scale = np.abs(g_ref).max()
     assert np.abs(g - g_ref).max() <= 5e-3 * scale, (np.abs(g - g_ref).max(), scale)
