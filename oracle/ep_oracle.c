@@ -35,6 +35,11 @@
  *    iteration (explicit in the old stress, implicit in the spin); products
  *    are formed where both factors live and averaged to the target location;
  *  - pseudo-time step 1, Vp = C dx_min, eta = eta_ve in Eq. PT1, L = L_max;
+ *  - optional advection of the old stress (the v_k d sigma_ij / dx_k term of
+ *    Eq. j1; the paper names its kernels adv1/adv2 in Fig. 1 but prints no
+ *    discretisation): once per increment, explicit first-order upwind
+ *    transport of the history deviator and pressure over dt with the
+ *    previous increment's converged velocity (see advect_history);
  *  - each iteration starts from the stress consistent with the start
  *    velocity (one pseudo step with no relaxation memory);
  *  - the stopping test takes the largest of the three equations' residuals,
@@ -88,6 +93,9 @@ typedef struct {
   long freeze_iter;   /* 0: never */
   double freeze_eps;
   int frozen;
+  /* advection of the old stress (Eq. j1), once per committed increment */
+  int advect;
+  long commits, adv_done;
   /* loading of the current increment (Eqs. A7-A9M) */
   double rate[3], dt;
   double *f[3];
@@ -553,6 +561,113 @@ static void accept_stress(or_grid *g) {
   for (int s = 0; s < n_shear_comp(g); ++s) memcpy(g->ts_k[s], g->ss[s], sizeof(double) * n_shear(g, s));
 }
 
+/* ------------------------------------------------------------------------ */
+/* Advection of the old stress: the v_k d sigma_ij / dx_k part of the        */
+/* Jaumann rate (Eq. j1).  The paper gives no discretisation; this reading:  */
+/* once per increment, before its iteration, every history component f      */
+/* (tau_hat at centres and at vertices/edges, p_hat at centres) becomes      */
+/*     f - dt * sum_e v_e(x_f) * D_e f                                        */
+/* with the previous increment's converged velocity v.  D_e is the upwind    */
+/* one-sided difference: (f[q] - f[q-1]) / h_e where v_e > 0, (f[q+1] -      */
+/* f[q]) / h_e where v_e < 0, and 0 where that neighbour lies outside the    */
+/* field (an inflow wall: zero gradient).  v_e(x_f) is the arithmetic mean   */
+/* of the nearest values of face component e: one value in each dimension   */
+/* where the field point and face e are staggered alike, the two neighbours */
+/* in each dimension where they are not.  Wall vertices/edges keep their    */
+/* zero shear stress (free slip).                                            */
+/* ------------------------------------------------------------------------ */
+
+/* staggering of a field point per dimension: 1 = on cell faces/vertices,
+ * 0 = at cell centres.  loc: -1 centres, c >= 0 shear component c. */
+static void stagger_of(const or_grid *g, int loc, int st[3]) {
+  st[0] = st[1] = st[2] = 0;
+  if (loc < 0) return;
+  if (g->ndim == 2) { st[0] = st[1] = 1; return; }
+  st[0] = loc != 2; st[1] = loc != 1; st[2] = loc != 0;
+}
+
+/* velocity component e at point (i, j, k) of staggering st */
+static double velocity_at(const or_grid *g, int e, const int st[3], int i, int j, int k) {
+  int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+  for (int d = 0; d < g->ndim; ++d) {
+    const int face_st = d == e;          /* face e sits on the grid lines of dimension e only */
+    if (face_st == st[d]) continue;
+    if (st[d]) { lo[d] = -1; hi[d] = 0; }  /* a grid line between cells q-1 and q */
+    else { lo[d] = 0; hi[d] = 1; }         /* a centre between grid lines q and q+1 */
+  }
+  int ex, ey, ez; face_dims(g, e, &ex, &ey, &ez);
+  double sum = 0.0;
+  int cnt = 0;
+  for (int c = lo[2]; c <= hi[2]; ++c)
+    for (int b = lo[1]; b <= hi[1]; ++b)
+      for (int a = lo[0]; a <= hi[0]; ++a) {
+        sum += g->v[e][((long)(k + c) * ey + (j + b)) * ex + (i + a)];
+        ++cnt;
+      }
+  return sum / cnt;
+}
+
+/* one field of extent (ex, ey, ez) and staggering st: out = advected f */
+static void advect_field(const or_grid *g, const double *f, double *out, int ex, int ey, int ez,
+                         const int st[3], double dt) {
+  const double h[3] = {g->dx, g->dy, g->dz};
+  const int ext[3] = {ex, ey, ez}, n[3] = {g->nx, g->ny, g->nz};
+  for (int k = 0; k < ez; ++k) for (int j = 0; j < ey; ++j) for (int i = 0; i < ex; ++i) {
+    const long id = ((long)k * ey + j) * ex + i;
+    const int q[3] = {i, j, k};
+    int wall = 0;
+    for (int d = 0; d < g->ndim; ++d) if (st[d] && (q[d] == 0 || q[d] == n[d])) wall = 1;
+    if (wall) { out[id] = f[id]; continue; }
+    double adv = 0.0;
+    for (int e = 0; e < g->ndim; ++e) {
+      const double ve = velocity_at(g, e, st, i, j, k);
+      const long step = e == 0 ? 1 : e == 1 ? ex : (long)ex * ey;
+      double D = 0.0;
+      if (ve > 0.0 && q[e] - 1 >= 0) D = (f[id] - f[id - step]) / h[e];
+      else if (ve < 0.0 && q[e] + 1 < ext[e]) D = (f[id + step] - f[id]) / h[e];
+      adv += ve * D;
+    }
+    out[id] = f[id] - dt * adv;
+  }
+}
+
+/* advect tau_hat and p_hat over dt with the velocity held in g->v */
+static int advect_history(or_grid *g, double dt) {
+  int st[3];
+  const long nc = n_centres(g);
+  long nmax = nc;
+  for (int c = 0; c < n_shear_comp(g); ++c) if (n_shear(g, c) > nmax) nmax = n_shear(g, c);
+  double *tmp = zalloc(nmax);
+  if (!tmp) return OR_ERR_OOM;
+  stagger_of(g, -1, st);
+  for (int d = 0; d <= g->ndim; ++d) {      /* normal components, then the pressure */
+    double *f = d < g->ndim ? g->tn[d] : g->p;
+    advect_field(g, f, tmp, g->nx, g->ny, g->nz, st, dt);
+    memcpy(f, tmp, sizeof(double) * nc);
+  }
+  for (int c = 0; c < n_shear_comp(g); ++c) {
+    int ex, ey, ez; shear_dims(g, c, &ex, &ey, &ez);
+    stagger_of(g, c, st);
+    advect_field(g, g->ts[c], tmp, ex, ey, ez, st, dt);
+    memcpy(g->ts[c], tmp, sizeof(double) * n_shear(g, c));
+  }
+  free(tmp);
+  return OR_OK;
+}
+
+/* Switch the per-increment advection of the old stress on or off. */
+int or_set_advection(or_grid *g, int on) {
+  g->advect = on != 0;
+  return OR_OK;
+}
+
+/* Advect the history now over dt with the velocity field g->v (the step
+ * or_apply_increment takes when advection is on). */
+int or_advect(or_grid *g, double dt) {
+  if (!(dt >= 0.0)) return OR_ERR_ARG;
+  return advect_history(g, dt);
+}
+
 /* Start of an increment (A0): the walls get the velocities of the pure-shear
  * (or any diagonal) background gradient, v_d = rate[d] * x_d (Eqs. A7-A9M);
  * the interior starts from the last converged field, or from the background
@@ -563,6 +678,11 @@ int or_apply_increment(or_grid *g, const double *rate, double dt, const double *
   if (!g->have_material || !(dt > 0.0)) return OR_ERR_ARG;
   for (int d = 0; d < 3; ++d) g->rate[d] = d < g->ndim ? rate[d] : 0.0;
   g->dt = dt;
+  if (g->advect && g->commits > g->adv_done) {   /* once per committed increment */
+    int r = advect_history(g, dt);
+    if (r != OR_OK) return r;
+    g->adv_done = g->commits;
+  }
   long off = 0;
   for (int d = 0; d < g->ndim; ++d) {
     long nf = n_face(g, d);
@@ -816,6 +936,7 @@ int or_commit(or_grid *g) {
     for (long i = 0; i < nf; ++i) { g->v[d][i] = g->vi[d][i]; g->u[d][i] += dt * g->vi[d][i]; }
   }
   g->in_increment = 0;
+  g->commits += 1;
   return OR_OK;
 }
 
