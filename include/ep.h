@@ -92,6 +92,13 @@ typedef struct {
    * never otherwise; 0 never freezes. */
   long long freeze_iter;
   double freeze_eps;    /* default 1e-4                                        */
+  /* advection of the old stress, the v_k d sigma_ij / dx_k term of the
+   * Jaumann rate (Eq. j1; Fig. 1's adv kernels): when 1, every increment
+   * after a committed one first transports tau_hat and p_hat over its dt with
+   * the last converged velocity (explicit first-order upwind; zero gradient
+   * at inflow walls; free-slip wall shear stays zero).  Stable for
+   * max|v| dt / dx_min <= 1 / ndim.  Default 0 (off). */
+  int advection;
 } ep_solver_opts;
 
 typedef struct {

@@ -31,7 +31,7 @@ FIELD_ID = {n: i for i, n in enumerate(FIELDS)}
 class SolverOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_longlong), ("n_chk", C.c_int),
                 ("c_cfl", C.c_double), ("xi", C.c_double), ("r_pt", C.c_double), ("jaumann", C.c_int),
-                ("freeze_iter", C.c_longlong), ("freeze_eps", C.c_double)]
+                ("freeze_iter", C.c_longlong), ("freeze_eps", C.c_double), ("advection", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -196,10 +196,11 @@ class Grid:
         return o
 
     def set_solver(self, tol=1e-8, max_iter=10000000, n_chk=100, c_cfl=None, xi=1.0, r_pt=0.5, jaumann=True,
-                   freeze_iter=-1, freeze_eps=1e-4):
+                   freeze_iter=-1, freeze_eps=1e-4, advection=False):
         """freeze_iter: frozen plasticity (Sec. 3.3) from this iteration on
         when eps_rel > freeze_eps; -1 the paper's rule (16 n_x above 10^6
-        cells), 0 never."""
+        cells), 0 never.  advection: transport the old stress with the last
+        converged velocity at the start of each increment (Eq. j1)."""
         o = self.default_solver()
         o.tol = tol
         o.max_iter = int(max_iter)
@@ -210,6 +211,7 @@ class Grid:
         o.jaumann = int(bool(jaumann))
         o.freeze_iter = int(freeze_iter)
         o.freeze_eps = float(freeze_eps)
+        o.advection = int(bool(advection))
         check(self.h, self._L.ep_set_solver(self.h, C.byref(o)))
 
     def apply_increment(self, a, dt, load_plane=LOAD_XY, body_force=None, use_warm_start=False):

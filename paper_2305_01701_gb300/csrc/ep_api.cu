@@ -65,6 +65,7 @@ struct ep_grid {
   // learned warm start
   double *vpp[3] = {};          // converged velocity of the increment before last
   int n_commits = 0;
+  int adv_done = 0;             // n_commits when the history was last advected
   double cmax = 1.0;
   ep_net *net = nullptr;
   float *wx = nullptr, *wy = nullptr;   // network input / output (cudaMalloc on attach)
@@ -391,6 +392,18 @@ ep_status prologue(ep_grid *h, const double *const dv[3]) {
   const Geo &g = h->g;
   cudaStream_t st = h->stream;
   launch_start_velocity(g, h->H, dv, h->dscal, h->started ? 1 : 0, h->L, st);
+  if (h->opts.advection && h->n_commits > h->adv_done) {
+    // transport the old stress with the last converged velocity H.v (Eq. j1);
+    // Tn64 / Ts64 / stp64 are free here (dv was consumed above)
+    const int nd = h->ndim, ns = n_shear(nd);
+    launch_advect(g, h->H, h->dscal, h->Tn64, h->Ts64, h->stp64, st);
+    for (int d = 0; d < nd; ++d)
+      CK(h, cudaMemcpyAsync(h->H.tn[d], h->Tn64[d], g.box * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    for (int c = 0; c < ns; ++c)
+      CK(h, cudaMemcpyAsync(h->H.ts[c], h->Ts64[c], g.box * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CK(h, cudaMemcpyAsync(h->H.p, h->stp64, g.box * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    h->adv_done = h->n_commits;
+  }
   launch_rotation_fields<double>(g, h->H, h->dscal, h->rq64, h->rd64, h->yc64, st);
   Stage<double> S = phys_stage(h, h->H.v0);
   launch_strain<double>(g, S, h->dscal, nullptr, st);
@@ -618,6 +631,7 @@ ep_status ep_default_solver(int ndim, ep_solver_opts *o) {
   o->jaumann = 1;
   o->freeze_iter = -1;
   o->freeze_eps = 1e-4;
+  o->advection = 0;
   return EP_OK;
 }
 

@@ -296,6 +296,83 @@ __global__ void k_warm_dv(Geo g, History H, const double *vp0, const double *vp1
   }
 }
 
+// ---- advection of the old stress (the v_k d sigma_ij / dx_k term, Eq. j1) ----
+// Once per increment: f <- f - dt * sum_e v_e D_e f for every history
+// component, with H.v the last converged velocity.  D_e is the first-order
+// upwind difference (the neighbour on the side the flow comes from; zero
+// where that neighbour is outside the field).  v_e at a field point is the
+// mean of the nearest face values of component e: in each dimension where
+// the point and face e are staggered alike one value, otherwise the two
+// neighbours.  st[d] = 1 marks a point on grid lines of dimension d.
+
+__device__ __forceinline__ double face_mean(const Geo &g, const double *v, int e, const int st[3], int i, int j,
+                                            int k) {
+  int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+  for (int d = 0; d < g.ndim; ++d) {
+    const int fs = d == e;  // face e lies on grid lines of dimension e only
+    if (fs == st[d]) continue;
+    if (st[d]) lo[d] = -1;  // grid-line point between cells q - 1 and q
+    else hi[d] = 1;         // centre between grid lines q and q + 1
+  }
+  double sum = 0.0;
+  int cnt = 0;
+  for (int c = lo[2]; c <= hi[2]; ++c)
+    for (int b = lo[1]; b <= hi[1]; ++b)
+      for (int a = lo[0]; a <= hi[0]; ++a) {
+        sum += v[g.idx(i + a, j + b, k + c)];
+        ++cnt;
+      }
+  return sum / cnt;
+}
+
+// advected value of f at (i, j, k) for a field of extent ext and staggering st
+__device__ double advected(const Geo &g, const History &H, const double *f, const int st[3], const int ext[3],
+                           int i, int j, int k, double dt) {
+  const long long e0 = g.idx(i, j, k);
+  const int q[3] = {i, j, k}, n[3] = {g.nx, g.ny, g.nz};
+  for (int d = 0; d < g.ndim; ++d)
+    if (st[d] && (q[d] == 0 || q[d] == n[d])) return f[e0];  // free-slip wall: shear stress stays
+  const double h[3] = {g.dx, g.dy, g.dz};
+  const long long step[3] = {1, g.px, g.plane};
+  double adv = 0.0;
+  for (int e = 0; e < g.ndim; ++e) {
+    const double ve = face_mean(g, H.v[e], e, st, i, j, k);
+    double D = 0.0;
+    if (ve > 0.0 && q[e] >= 1) D = (f[e0] - f[e0 - step[e]]) / h[e];
+    else if (ve < 0.0 && q[e] + 1 < ext[e]) D = (f[e0 + step[e]] - f[e0]) / h[e];
+    adv += ve * D;
+  }
+  return f[e0] - dt * adv;
+}
+
+__global__ void k_advect(Geo g, History H, const Scal *sc, double *tn0, double *tn1, double *tn2, double *ts0,
+                         double *ts1, double *ts2, double *pout) {
+  const Pos3 q = pos3(g);
+  if (!q.in) return;
+  const int i = q.i, j = q.j, k = q.k;
+  const long long e = q.e;
+  const double dt = sc->dt;
+  const bool centre = i < g.nx && j < g.ny && k < g.nz;
+  const int sc0[3] = {0, 0, 0}, extc[3] = {g.nx, g.ny, g.nz};
+  double *tno[3] = {tn0, tn1, tn2};
+  for (int d = 0; d < g.ndim; ++d)
+    tno[d][e] = centre ? advected(g, H, H.tn[d], sc0, extc, i, j, k, dt) : H.tn[d][e];
+  pout[e] = centre ? advected(g, H, H.p, sc0, extc, i, j, k, dt) : H.p[e];
+  double *tso[3] = {ts0, ts1, ts2};
+  const int ns = g.ndim == 3 ? 3 : 1;
+  for (int c = 0; c < ns; ++c) {
+    int st[3], ext[3];
+    if (g.ndim == 2) {
+      st[0] = 1; st[1] = 1; st[2] = 0;
+    } else {
+      st[0] = c != 2; st[1] = c != 1; st[2] = c != 0;
+    }
+    ext[0] = g.nx + st[0]; ext[1] = g.ny + st[1]; ext[2] = g.nz + st[2];
+    const bool in = i < ext[0] && j < ext[1] && k < ext[2];
+    tso[c][e] = in ? advected(g, H, H.ts[c], st, ext, i, j, k, dt) : H.ts[c][e];
+  }
+}
+
 }  // namespace
 
 void launch_warm_scale(const Geo &g, const History &H, const double *const vp[3], unsigned long long *slot,
@@ -370,6 +447,12 @@ void launch_pack(const double *box, double *dst, int ex, int ey, int ez, int px,
 void launch_unpack(const double *src, double *box, int ex, int ey, int ez, int px, int py, cudaStream_t st) {
   long long n = (long long)ex * ey * ez;
   k_unpack<<<blocks_for(n), kThreads, 0, st>>>(src, box, ex, ey, ez, px, py);
+}
+
+void launch_advect(const Geo &g, const History &H, const Scal *sc, double *const tn_out[3], double *const ts_out[3],
+                   double *p_out, cudaStream_t st) {
+  k_advect<<<blocks_for(g.box), kThreads, 0, st>>>(g, H, sc, tn_out[0], tn_out[1], tn_out[2], ts_out[0], ts_out[1],
+                                                   ts_out[2], p_out);
 }
 
 template void launch_rotation_fields<float>(const Geo &, const History &, const Scal *, float *const[3],

@@ -233,6 +233,8 @@ void launch_commit(const Geo &g, const History &H, const double *const Tn64[3], 
 template <typename Td, typename Ts>
 void launch_convert(Td *dst, const Ts *src, long long n, cudaStream_t st);
 void launch_line_integrals(const Geo &g, const History &H, double *out2, cudaStream_t st);
+void launch_advect(const Geo &g, const History &H, const Scal *sc, double *const tn_out[3], double *const ts_out[3],
+                   double *p_out, cudaStream_t st);
 void launch_pack(const double *box, double *dst, int ex, int ey, int ez, int px, int py, cudaStream_t st);
 void launch_warm_scale(const Geo &g, const History &H, const double *const vp[3], unsigned long long *slot,
                        cudaStream_t st);

@@ -192,11 +192,11 @@ def test_fp64_body_force_manufactured(P):
     del sp
 
 
-def run_fp32_vs_oracle(P, s, increments, gpu_tol=1e-6, oracle_tol=1e-10):
+def run_fp32_vs_oracle(P, s, increments, gpu_tol=1e-6, oracle_tol=1e-10, **solver):
     """FP32 mixed GPU solve at its tolerance against a tightly converged FP64
     oracle: the worst L-infinity-normalised error of each field."""
-    g = gpu_grid(P, s, P.FP32_MIXED, tol=gpu_tol, max_iter=400000)
-    o = O.from_setup(s, tol=oracle_tol)
+    g = gpu_grid(P, s, P.FP32_MIXED, tol=gpu_tol, max_iter=400000, **solver)
+    o = O.from_setup(s, tol=oracle_tol, **solver)
     fields = FIELDS_2D if s.ndim == 2 else FIELDS_3D
     worst = {}
     for inc in range(1, increments + 1):
@@ -224,6 +224,46 @@ def test_fp32_mixed_within_stated_bounds_2d(P):
 def test_fp32_mixed_within_stated_bounds_3d(P):
     s = E.config(3, n=(16, 15, 14), inclusion_radius=0.15)
     worst = run_fp32_vs_oracle(P, s, 7)
+    for f in ("txx", "tyy", "tzz", "txy", "txz", "tyz", "p"):
+        assert worst[f] <= 1e-5, (f, worst[f])
+    assert worst["epl"] <= 1e-4, worst["epl"]
+
+
+def test_advection_fp64_parity_2d(P):
+    """Advection of the old stress (Eq. j1) on: every increment after the
+    first transports tau_hat and p_hat with the last converged velocity.
+    Same iterations and fields within 1e-10 of the oracle through first
+    yield; one increment applied twice on the GPU side only (advected once)."""
+    s = E.config(1, n=(40, 33), tol=1e-9)
+    g = gpu_grid(P, s, P.FP64, advection=True)
+    o = O.from_setup(s, advection=True)
+    for inc in range(1, 11):
+        g.apply_increment_rates(rates_of(s), s.dt)
+        if inc == 6:
+            g.apply_increment_rates(rates_of(s), s.dt)
+        ig = g.solve_increment()
+        o.apply_increment(rates_of(s), s.dt)
+        io = o.solve_increment()
+        assert ig["iters"] == io["iters"], (inc, ig["iters"], io["iters"])
+        sc = group_scales(o, FIELDS_2D)
+        for f in FIELDS_2D:
+            e = rel_err(g.get(f), o.get(f), sc[f])
+            assert e <= 1e-10, (inc, f, e)
+    assert io["n_plastic"] > 0
+    g.close()
+
+
+@pytest.mark.parametrize("variant", [0, 3])
+def test_advection_fp64_parity_3d(P, variant):
+    """Advection on in 3D (x-z pure shear) with the staged and the register
+    sweeps: every history component incl. the three edge families."""
+    s = E.config(3, n=(17, 13, 11), tol=1e-9, precision="fp64", inclusion_radius=0.2)
+    run_pair_kernel(P, s, 7, variant, 4, advection=True)
+
+
+def test_advection_fp32_mixed_within_stated_bounds_3d(P):
+    s = E.config(3, n=(16, 15, 14), inclusion_radius=0.15)
+    worst = run_fp32_vs_oracle(P, s, 7, advection=True)
     for f in ("txx", "tyy", "tzz", "txy", "txz", "tyz", "p"):
         assert worst[f] <= 1e-5, (f, worst[f])
     assert worst["epl"] <= 1e-4, worst["epl"]
