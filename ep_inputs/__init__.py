@@ -102,6 +102,43 @@ class Setup:
         return cohesion_field(self.n, self.L[: self.ndim], self.c0, self.noise, self.seed,
                               self.inclusion_radius, self.inclusion_centre[: self.ndim])
 
+    def initial_pressure(self):
+        """The initial (history) pressure of the setup, or None (zero)."""
+        a = self.extra.get("pressure_anomaly")
+        if a is None:
+            return None
+        return pressure_anomaly(self.n, self.L[: self.ndim], a["value"], a["radius"])
+
+
+def pressure_anomaly(n, L, value, radius, centre=None):
+    """Initial pressure: ``value`` at cells whose centre lies within ``radius``
+    of ``centre`` (default the box centre), 0 elsewhere; shape as
+    :func:`cohesion_field`."""
+    ndim = len(n)
+    centre = centre if centre is not None else [0.0] * ndim
+    axes = cell_centres(n, L)
+    grids = np.meshgrid(*reversed(axes), indexing="ij")
+    r2 = np.zeros(tuple(reversed(n)))
+    for d in range(ndim):
+        r2 += (grids[ndim - 1 - d] - centre[d]) ** 2
+    return np.ascontiguousarray(np.where(r2 <= radius ** 2, value, 0.0), dtype=np.float64)
+
+
+def anomaly_setup(n=(383, 191), **overrides) -> Setup:
+    """The box of the paper's symmetry study (Sec. 4.3, "Symmetry versus
+    non-symmetry"): a 2:1 plane-strain box, uniform G = 1 and cohesion
+    c = 0.2e-2 G (no noise, no inclusion), Deborah number 1e6 (mu_s = 1e6 G t,
+    the elastic limit), no Jaumann term, and a circular pressure anomaly
+    p = c / 2 at the centre.  The paper prints no anomaly radius; 0.05 L_y is
+    used.  Solver settings go in ``extra`` (``jaumann``)."""
+    c = 2e-3
+    s = Setup("2d-anomaly", 2, tuple(n), L=(2.0, 1.0, 1.0), mu_s=1e6, c0=c, inclusion_radius=0.0, noise=0.0,
+              seed=6000, increments=180, tol=1e-10)
+    s.extra = {"pressure_anomaly": {"value": 0.5 * c, "radius": 0.05}, "jaumann": False}
+    for k, v in overrides.items():
+        setattr(s, k, v)
+    return s
+
 
 def config(index: int, **overrides) -> Setup:
     """The five named workloads (seeds: index * 1000 + instance).

@@ -269,6 +269,33 @@ def test_advection_fp32_mixed_within_stated_bounds_3d(P):
     assert worst["epl"] <= 1e-4, worst["epl"]
 
 
+def test_pressure_anomaly_fp64_parity_2d(P):
+    """The paper's symmetry-study box (2:1, uniform G and c, De = 1e6, no
+    Jaumann term) seeded by an initial circular pressure anomaly p = c/2,
+    written into the history on both sides: the anomaly is out of equilibrium,
+    so the first increments iterate; same iterations and fields within 1e-10
+    through first yield."""
+    s = E.anomaly_setup(n=(96, 48), tol=1e-10)
+    g = gpu_grid(P, s, P.FP64, jaumann=False)
+    o = O.from_setup(s, jaumann=False)
+    p0 = s.initial_pressure()
+    g.set("p", p0)
+    o.set("p", p0)
+    for inc in range(1, 9):
+        g.apply_increment_rates(rates_of(s), s.dt)
+        ig = g.solve_increment()
+        o.apply_increment(rates_of(s), s.dt)
+        io = o.solve_increment()
+        assert ig["iters"] == io["iters"], (inc, ig["iters"], io["iters"])
+        assert ig["n_plastic"] == io["n_plastic"], (inc, ig["n_plastic"], io["n_plastic"])
+        sc = group_scales(o, FIELDS_2D)
+        for f in FIELDS_2D:
+            e = rel_err(g.get(f), o.get(f), sc[f])
+            assert e <= 1e-10, (inc, f, e)
+    assert io["n_plastic"] > 0
+    g.close()
+
+
 def test_not_converged_keeps_state_and_reports(P):
     s = E.config(1, n=(32, 32))
     g = gpu_grid(P, s, P.FP64, max_iter=200, n_chk=100, tol=1e-14)
