@@ -278,7 +278,7 @@ def timed_steps(torch, P, g, s, stream, steps, barrier):
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # dominant kernel from one ncu capture of the benchmark command, by kernel and
 # box size; the entry must be dropped when the kernel changes.
-NCU_TRAFFIC = {("k_fused3d_reg", 127): 268.0e6}
+NCU_TRAFFIC = {("k_fused3d_reg", 127): 271.8e6}
 
 
 def kernel_names(ktimes, kernel):

@@ -71,7 +71,13 @@ __global__ void __launch_bounds__(SW *SWARPS) k_fused2d_strip(const Inst2<T> *in
     const T *u0 = I.u[b][0], *u1 = I.u[b][1];
 
     auto at = [&](int row) { return (long long)row * px + gi; };
-    auto ld = [&](const T *p, int row) -> T { return (xin && row >= 0 && row < py) ? p[at(row)] : (T)0; };
+    // FP32 loads read the nearest in-box column and row without a test: a
+    // value outside the box only ever enters guarded expressions
+    const long long gic = min(max(gi, 0), g.px - 1);
+    auto ld = [&](const T *p, int row) -> T {
+      if constexpr (sizeof(T) == 4) return p[(long long)min(max(row, 0), py - 1) * px + gic];
+      else return (xin && row >= 0 && row < py) ? p[at(row)] : (T)0;
+    };
 
     // inputs two rows ahead (vertex / face arrays of row r, centre arrays of
     // row r - 1): `next` holds row t + 1, `after` row t + 2
@@ -140,10 +146,15 @@ __global__ void __launch_bounds__(SW *SWARPS) k_fused2d_strip(const Inst2<T> *in
           if (frozen) {
             s_1 = I.s[e];   // frozen plasticity: the held scale (Sec. 3.3)
           } else {
-            const T sj = sqrt(J2);
             T Y = Acoef * pr + yc;
             Y = Y > (T)0 ? Y : (T)0;
-            s_1 = sj > Y ? Y / sj : (T)1;
+            if constexpr (sizeof(T) == 4) {
+              // FP32: compare squares, scale with the reciprocal square root
+              s_1 = J2 > Y * Y ? Y * rsqrtf(J2) : (T)1;
+            } else {
+              const T sj = sqrt(J2);
+              s_1 = sj > Y ? Y / sj : (T)1;
+            }
           }
           const T n0 = s_1 * c0, n1 = s_1 * c1;
           sxx_1 = n0 - pr;

@@ -16,7 +16,16 @@
 // Plane t of the march computes spins at plane t, edge trials at face t and
 // plane t-1, centres t-1, edges t-1 and velocities t-2.  Four block barriers
 // separate the steps of a plane.
+// Instruction count (the kernel is issue-bound, not bandwidth-bound):
+//   * blocks whose whole window lies inside the domain run a copy of the body
+//     in which the domain-boundary tests are compile-time true;
+//   * FP32 loads take a clamped in-box address and no test: a value read
+//     outside the box only ever enters guarded expressions;
+//   * the march is unrolled by two planes, so the shared-memory slot of each
+//     copy is a compile-time constant.
 #include <math.h>
+
+#include <type_traits>
 
 #include "ep_internal.cuh"
 
@@ -56,22 +65,31 @@ struct Args {
   const T *s;   // centre return scales (read when plasticity is frozen)
 };
 
-template <typename T, int H>
-__global__ void __launch_bounds__(WX *H, 1)
-    k_fused3d_reg(const Args<T> A, Geo g, const Scal *sc, const DevInfo *di, int kz) {
-  if (di != nullptr && *(volatile const int *)&di->done != 0) return;
-  const bool frozen = di != nullptr && di->frozen;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+// INT: every column of the block's window lies strictly inside the domain
+// (1 <= x, y index <= n - 1), so the domain-boundary tests fold away.
+template <typename T, int H, bool INT>
+__device__ __forceinline__ void reg_body(const Args<T> &A, const Geo &g, const Scal *sc, bool frozen, int kz,
+                                         unsigned char *smem_raw) {
   SmemR<T, H> &S = *reinterpret_cast<SmemR<T, H> *>(smem_raw);
   constexpr int W = WX;
   const int a = threadIdx.x & 31, b = threadIdx.x >> 5;
   const int i0 = blockIdx.x * OX, j0 = blockIdx.y * (H - 4);
   const int gi = i0 - 2 + a, gj = j0 - 2 + b;
   const int kb = blockIdx.z * kz, ke = min(kb + kz, g.pz);
-  const int nx = g.nx, ny = g.ny, nz = g.nz, pz = g.pz;
+  const int nz = g.nz, pz = g.pz;
   const long long px = g.px, plane = g.plane;
-  const bool inb = gi >= 0 && gi < g.px && gj >= 0 && gj < g.py;
-  const long long col = inb ? (long long)gj * px + gi : 0;  // this column's offset in a plane
+  const bool inb = INT || (gi >= 0 && gi < g.px && gj >= 0 && gj < g.py);
+  const bool gx1 = INT || (gi >= 1 && gi <= g.nx - 1), gy1 = INT || (gj >= 1 && gj <= g.ny - 1);
+  const bool gx0 = INT || (gi >= 0 && gi < g.nx), gy0 = INT || (gj >= 0 && gj < g.ny);
+  const bool gxl = INT || gi < g.nx, gyl = INT || gj < g.ny;
+  // this column's offset in a plane.  FP32 clamps it into the box so that
+  // loads need no test (a value outside the box only ever enters guarded
+  // expressions); every store and the frozen-scale read are guarded by
+  // in-box tests, where the clamped offset is the exact one.  FP64 keeps the
+  // tested loads (fewer registers).
+  const long long col = sizeof(T) == 4 ? (long long)min(max(gj, 0), g.py - 1) * px + min(max(gi, 0), g.px - 1)
+                                       : (inb ? (long long)gj * px + gi : 0);
+
   const bool out_col = a >= 2 && a < W - 2 && b >= 2 && b < H - 2;
   const T rdx = (T)g.rdx, rdy = (T)g.rdy, rdz = (T)g.rdz;
   const T two_eta = (T)sc->two_eta, bt = (T)sc->bt, ob = (T)1 - bt;
@@ -91,7 +109,8 @@ __global__ void __launch_bounds__(WX *H, 1)
   }
 
   auto ld = [&](const T *p, int lev) -> T {
-    return (inb && lev >= 0 && lev < pz) ? __ldg(p + (long long)lev * plane + col) : (T)0;
+    if constexpr (sizeof(T) == 4) return __ldg(p + (long long)min(max(lev, 0), pz - 1) * plane + col);
+    else return (inb && lev >= 0 && lev < pz) ? __ldg(p + (long long)lev * plane + col) : (T)0;
   };
 
   // inputs of the next plane (loaded one plane ahead)
@@ -119,8 +138,10 @@ __global__ void __launch_bounds__(WX *H, 1)
   T nxy_2 = 0, nxz_2 = 0, nyz_2 = 0;           // edge stress, level t-2
 
   prefetch(kb - 2);
-  for (int t = kb - 2; t < ke + 2; ++t) {
-    const int sl = t & 1, sl1 = sl ^ 1;  // plane slots of t and t - 1
+  // the march unrolled by two planes: the slot parity of each copy is a
+  // compile-time constant
+  auto plane_step = [&](const int t, auto slc) {
+    constexpr int sl = decltype(slc)::value, sl1 = sl ^ 1;  // plane slots of t and t - 1
     // ---- 0. take this plane's inputs, publish the row-exchanged ones ----
     u0_2 = u0_1; u1_2 = u1_1; u2_2 = u2_1;
     u0_1 = u0; u1_1 = u1; u2_1 = u2;
@@ -141,15 +162,15 @@ __global__ void __launch_bounds__(WX *H, 1)
     {
       const T u0_ym = S.u0.r[rb - 1][a], u2_ym = S.u2.r[rb - 1][a];
       const T u1_xm = xm(u1), u2_xm = xm(u2);
-      if (a >= 1 && b >= 1 && t >= 0 && t < nz && gi >= 1 && gi <= nx - 1 && gj >= 1 && gj <= ny - 1) {
+      if (a >= 1 && b >= 1 && t >= 0 && t < nz && gx1 && gy1) {
         const T x = (u0 - u0_ym) * rdy, y = (u1 - u1_xm) * rdx;
         exy = hf * (x + y); oxy = hf * (x - y);
       }
-      if (a >= 1 && t >= 1 && t <= nz - 1 && gi >= 1 && gi <= nx - 1 && gj >= 0 && gj < ny) {
+      if (a >= 1 && t >= 1 && t <= nz - 1 && gx1 && gy0) {
         const T x = (u0 - u0_1) * rdz, y = (u2 - u2_xm) * rdx;
         exz = hf * (x + y); oxz = hf * (x - y);
       }
-      if (b >= 1 && t >= 1 && t <= nz - 1 && gi >= 0 && gi < nx && gj >= 1 && gj <= ny - 1) {
+      if (b >= 1 && t >= 1 && t <= nz - 1 && gx0 && gy1) {
         const T x = (u1 - u1_1) * rdz, y = (u2 - u2_ym) * rdy;
         eyz = hf * (x + y); oyz = hf * (x - y);
       }
@@ -184,7 +205,7 @@ __global__ void __launch_bounds__(WX *H, 1)
       const T pyz_1_yp = S.pyz[sl1].r[rb + 1][a], pyz_yp = S.pyz[sl].r[rb + 1][a];
 
       if (b < H - 1 && t >= 1 && t <= nz - 1)
-      if (a >= 1 && gi >= 1 && gi <= nx - 1 && gj >= 0 && gj < ny) {
+      if (a >= 1 && gx1 && gy0) {
         const T dzx = qr * (rd1_1_xm + rd1_1 + rd1_xm + rd1);
         const T Tyz = qr * (rq2_xm + rq2 + rq2_yp_xm + rq2_yp);
         const T Wyz = qr * (oyz_xm + oyz + oyz_yp_xm + oyz_yp);
@@ -194,7 +215,7 @@ __global__ void __launch_bounds__(WX *H, 1)
         tsxz = bt * soxz + ob * tr;
       }
       if (b >= 1 && t >= 1 && t <= nz - 1)
-      if (a < W - 1 && gi >= 0 && gi < nx && gj >= 1 && gj <= ny - 1) {
+      if (a < W - 1 && gx0 && gy1) {
         const T dzy = qr * ((rd1_1_ym - rd0_1_ym) + (rd1_1 - rd0_1) + (rd1_ym - rd0_ym) + (rd1 - rd0));
         const T Txy = qr * (rq0_1 + rq0_1_xp + rq0 + rq0_xp);
         const T Wxy = qr * (oxy_1 + oxy_1_xp + oxy + oxy_xp);
@@ -204,7 +225,7 @@ __global__ void __launch_bounds__(WX *H, 1)
         tsyz = bt * soyz + ob * tr;
       }
       if (b >= 1 && lc >= 0 && lc < nz)
-      if (a >= 1 && gi >= 1 && gi <= nx - 1 && gj >= 1 && gj <= ny - 1) {
+      if (a >= 1 && gx1 && gy1) {
         const T dyx = qr * (rd0_1_ym_xm + rd0_1_ym + rd0_1_xm + rd0_1);
         const T Tyz = qr * (rq2_1_xm + rq2_1 + rq2_xm + rq2);
         const T Wyz = qr * (oyz_1_xm + oyz_1 + oyz_xm + oyz);
@@ -214,7 +235,7 @@ __global__ void __launch_bounds__(WX *H, 1)
         tsxy = bt * soxy + ob * tr;
       }
       if (b < H - 1 && lc >= 0 && lc < nz)
-      if (a < W - 1 && gi >= 0 && gi < nx && gj >= 0 && gj < ny) {
+      if (a < W - 1 && gx0 && gy0) {
         exx = (u0_1_xp - u0_1) * rdx;
         eyy = (u1_1_yp - u1_1) * rdy;
         ezz = (u2 - u2_1) * rdz;
@@ -241,7 +262,7 @@ __global__ void __launch_bounds__(WX *H, 1)
       const T tsxz_1_xp = xp(tsxz_1), tsxz_xp = xp(tsxz);
       const T tsyz_1_yp = S.tsyz[sl1].r[rb + 1][a], tsyz_yp = S.tsyz[sl].r[rb + 1][a];
       if (b >= 1 && b < H - 1 && lc >= 0 && lc < nz)
-      if (a >= 1 && a < W - 1 && gi >= 0 && gi < nx && gj >= 0 && gj < ny) {
+      if (a >= 1 && a < W - 1 && gx0 && gy0) {
         const T div = exx + eyy + ezz;
         const T pr = bp * sop + obp * (pb - KDt * div);
         const T txy = qr * (tsxy + tsxy_xp + tsxy_yp + tsxy_yp_xp);
@@ -280,11 +301,11 @@ __global__ void __launch_bounds__(WX *H, 1)
       const T s_1_ym = S.s[sl1].r[rb - 1][a], s_2_ym = S.s[sl].r[rb - 1][a];
       const T s_1_ym_xm = xm(s_1_ym);
       const bool inner = a >= 2 && a < W - 1 && b >= 2 && b < H - 1;
-      if (inner && lc >= 0 && lc < nz && gi >= 1 && gi <= nx - 1 && gj >= 1 && gj <= ny - 1)
+      if (inner && lc >= 0 && lc < nz && gx1 && gy1)
         nxy_1 = qr * (s_1_ym_xm + s_1_ym + s_1_xm + s_1) * tsxy;
-      if (inner && lc >= 1 && lc <= nz - 1 && gi >= 1 && gi <= nx - 1 && gj >= 0 && gj < ny)
+      if (inner && lc >= 1 && lc <= nz - 1 && gx1 && gy0)
         nxz_1 = qr * (s_2_xm + s_2 + s_1_xm + s_1) * tsxz_1;
-      if (inner && lc >= 1 && lc <= nz - 1 && gi >= 0 && gi < nx && gj >= 1 && gj <= ny - 1)
+      if (inner && lc >= 1 && lc <= nz - 1 && gx0 && gy1)
         nyz_1 = qr * (s_2_ym + s_2 + s_1_ym + s_1) * tsyz_1;
       if (out_col && lc >= kb && lc < ke && inb) {
         const long long e = (long long)lc * plane + col;
@@ -302,19 +323,19 @@ __global__ void __launch_bounds__(WX *H, 1)
         const T nyz_2_yp = S.nyz[sl].r[rb + 1][a];
         const long long e = (long long)lu * plane + col;
         T un = u0_2;
-        if (gi >= 1 && gi <= nx - 1 && gj < ny && lu < nz) {
+        if (gx1 && gyl && lu < nz) {
           const T R = (sxx_2 - sxx_2_xm) * rdx + (nxy_2_yp - nxy_2) * rdy + (nxz_1 - nxz_2) * rdz;
           un = u0_2 + vs * R;
         }
         A.uo[0][e] = un;
         un = u1_2;
-        if (gj >= 1 && gj <= ny - 1 && gi < nx && lu < nz) {
+        if (gy1 && gxl && lu < nz) {
           const T R = (syy_2 - syy_2_ym) * rdy + (nxy_2_xp - nxy_2) * rdx + (nyz_1 - nyz_2) * rdz;
           un = u1_2 + vs * R;
         }
         A.uo[1][e] = un;
         un = u2_2;
-        if (lu >= 1 && lu <= nz - 1 && gi < nx && gj < ny) {
+        if (lu >= 1 && lu <= nz - 1 && gxl && gyl) {
           const T R = (szz_2 - szz_3) * rdz + (nxz_2_xp - nxz_2) * rdx + (nyz_2_yp - nyz_2) * rdy;
           un = u2_2 + vs * R;
         }
@@ -329,7 +350,25 @@ __global__ void __launch_bounds__(WX *H, 1)
     s_2 = s_1;
     sxx_2 = sxx_1; syy_2 = syy_1; szz_3 = szz_2; szz_2 = szz_1;
     nxy_2 = nxy_1; nxz_2 = nxz_1; nyz_2 = nyz_1;
+  };
+  int t = kb - 2;
+  for (; t + 1 < ke + 2; t += 2) {
+    plane_step(t, std::integral_constant<int, 0>{});
+    plane_step(t + 1, std::integral_constant<int, 1>{});
   }
+  if (t < ke + 2) plane_step(t, std::integral_constant<int, 0>{});
+}
+
+template <typename T, int H>
+__global__ void __launch_bounds__(WX *H, 1)
+    k_fused3d_reg(const Args<T> A, Geo g, const Scal *sc, const DevInfo *di, int kz) {
+  if (di != nullptr && *(volatile const int *)&di->done != 0) return;
+  const bool frozen = di != nullptr && di->frozen;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int i0 = blockIdx.x * OX, j0 = blockIdx.y * (H - 4);
+  const bool interior = i0 - 2 >= 1 && i0 + WX - 3 <= g.nx - 1 && j0 - 2 >= 1 && j0 + H - 3 <= g.ny - 1;
+  if (interior) reg_body<T, H, true>(A, g, sc, frozen, kz, smem_raw);
+  else reg_body<T, H, false>(A, g, sc, frozen, kz, smem_raw);
 }
 
 template <typename T>

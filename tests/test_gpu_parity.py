@@ -192,10 +192,12 @@ def test_fp64_body_force_manufactured(P):
     del sp
 
 
-def run_fp32_vs_oracle(P, s, increments, gpu_tol=1e-6, oracle_tol=1e-10, **solver):
+def run_fp32_vs_oracle(P, s, increments, gpu_tol=1e-6, oracle_tol=1e-10, kernel=None, **solver):
     """FP32 mixed GPU solve at its tolerance against a tightly converged FP64
     oracle: the worst L-infinity-normalised error of each field."""
     g = gpu_grid(P, s, P.FP32_MIXED, tol=gpu_tol, max_iter=400000, **solver)
+    if kernel is not None:
+        g.set_kernel(*kernel)
     o = O.from_setup(s, tol=oracle_tol, **solver)
     fields = FIELDS_2D if s.ndim == 2 else FIELDS_3D
     worst = {}
@@ -216,6 +218,18 @@ def test_fp32_mixed_within_stated_bounds_2d(P):
     strain within 1e-4 of the FP64 oracle (L-infinity normalised)."""
     s = E.config(1, n=(48, 40))
     worst = run_fp32_vs_oracle(P, s, 8)
+    for f in ("txx", "tyy", "txy", "p"):
+        assert worst[f] <= 1e-5, (f, worst[f])
+    assert worst["epl"] <= 1e-4, worst["epl"]
+
+
+@pytest.mark.parametrize("tile", [0, 3, 4])
+def test_fp32_fused2d_within_stated_bounds(P, tile):
+    """The fused 2D kernels in FP32 (block tile, warp strips of 64 and 32
+    rows; the strips take untested clamped loads and the reciprocal-square-
+    root return) against the FP64 oracle within the stated bounds."""
+    s = E.config(1, n=(60, 90), inclusion_radius=0.08)
+    worst = run_fp32_vs_oracle(P, s, 6, kernel=(P.KERNEL_FUSED, tile))
     for f in ("txx", "tyy", "txy", "p"):
         assert worst[f] <= 1e-5, (f, worst[f])
     assert worst["epl"] <= 1e-4, worst["epl"]
