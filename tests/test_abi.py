@@ -58,3 +58,37 @@ def test_layout_of_fields_matches_the_oracle():
                 continue
             assert _native.field_shape(nd, n, f) == O.field_shape(nd, n, f), f
         assert _native.FIELD_ID == {k: v for k, v in O.FIELD_ID.items() if k in _native.FIELD_ID}
+
+
+def _c_layout(struct, fields):
+    """sizeof and offsetof of a struct of include/ep.h, from a C compiler."""
+    import shutil
+    import subprocess
+    import tempfile
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    body = 'printf("%%zu", sizeof(%s));' % struct
+    body += "".join('printf(" %%zu", offsetof(%s, %s));' % (struct, f) for f in fields)
+    src = ('#include <stddef.h>\n#include <stdio.h>\n#include "ep.h"\n'
+           "int main(void) { %s printf(\"\\n\"); return 0; }\n" % body)
+    with tempfile.TemporaryDirectory() as d:
+        c, exe = os.path.join(d, "l.c"), os.path.join(d, "l")
+        open(c, "w").write(src)
+        subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split()
+    return int(out[0]), [int(x) for x in out[1:]]
+
+
+@pytest.mark.parametrize("cls,struct", [("SolverOpts", "ep_solver_opts"), ("SolveInfo", "ep_solve_info")])
+def test_binding_structs_match_the_header_layout(cls, struct):
+    """The ctypes mirrors of the option and result structs have the C
+    compiler's size and field offsets (a field added on one side only, or in
+    another order, fails here rather than as garbage on the GPU)."""
+    from paper_2305_01701_gb300 import _native
+    import ctypes
+    S = getattr(_native, cls)
+    names = [n for n, _ in S._fields_]
+    size, offs = _c_layout(struct, names)
+    assert ctypes.sizeof(S) == size
+    assert [getattr(S, n).offset for n in names] == offs
