@@ -29,6 +29,11 @@ constexpr int kThreads = 256;
 
 // max that keeps a NaN from either side (fmax would drop it)
 __device__ __forceinline__ double maxn(double a, double b) { return (a > b || a != a) ? a : b; }
+// the same in the sweep's type: check-iteration maxima are formed in T and
+// widened once per thread (FP64 arithmetic is scarce on this part; the
+// difference of two nearby FP32 values is exact in FP32)
+template <typename T>
+__device__ __forceinline__ T maxt(T a, T b) { return (a > b || a != a) ? a : b; }
 
 __device__ __forceinline__ unsigned long long abs_bits(double v) {
   return (unsigned long long)__double_as_longlong(fabs(v));
@@ -220,7 +225,7 @@ __global__ void __launch_bounds__(kThreads) k_return_centres(Geo g, Stage<T> S, 
   const long long c = q.e, px = g.px, pl = g.plane;
   const bool act = q.in && i < g.nx && j < g.ny && (ND == 2 || k < g.nz);
   const bool frozen = di != nullptr && di->frozen;
-  double sig = 0.0, dtau = 0.0, dp = 0.0;
+  T sig = 0, dtau = 0, dp = 0;
   if (act) {
     const T qr = (T)0.25;
     T div = (S.u[0][c + 1] - S.u[0][c]) * (T)g.rdx + (S.u[1][c + px] - S.u[1][c]) * (T)g.rdy;
@@ -257,23 +262,23 @@ __global__ void __launch_bounds__(kThreads) k_return_centres(Geo g, Stage<T> S, 
       T t = s * tn[d];
       S.snn[d][c] = t;
       if (check) {
-        sig = maxn(sig, fabs((double)t - (double)p));
+        sig = maxt(sig, (T)fabs(t - p));
         if (S.relax) {
-          dtau = maxn(dtau, fabs((double)t - (double)S.cn[d][c]));
+          dtau = maxt(dtau, (T)fabs(t - S.cn[d][c]));
           S.cn[d][c] = t;
         }
       }
     }
     if (check && S.relax) {
-      dp = fabs((double)p - (double)S.cp[c]);
+      dp = (T)fabs(p - S.cp[c]);
       S.cp[c] = p;
     }
-    if (check && (isnan((double)s) || isnan((double)p))) sig = nan("");
+    if (check && (isnan(s) || isnan(p))) sig = (T)NAN;
   }
   if (check && di) {
-    block_max(abs_bits(sig), &di->red[RED_SIG]);
-    block_max(abs_bits(dtau), &di->red[RED_DTAU]);
-    block_max(abs_bits(dp), &di->red[RED_DP]);
+    block_max(abs_bits((double)sig), &di->red[RED_SIG]);
+    block_max(abs_bits((double)dtau), &di->red[RED_DTAU]);
+    block_max(abs_bits((double)dp), &di->red[RED_DP]);
   }
 }
 
@@ -285,7 +290,7 @@ __global__ void __launch_bounds__(kThreads) k_return_edges(Geo g, Stage<T> S, co
   const Pos q = position(g);
   const int i = q.i, j = q.j, k = q.k, nx = g.nx, ny = g.ny, nz = g.nz;
   const long long e = q.e, px = g.px, pl = g.plane;
-  double sig = 0.0, dtau = 0.0;
+  T sig = 0, dtau = 0;
   const T qr = (T)0.25;
   if (q.in && i <= nx && j <= ny && k <= (ND == 3 ? nz : 0)) {
     if (ND == 2) {
@@ -294,9 +299,9 @@ __global__ void __launch_bounds__(kThreads) k_return_edges(Geo g, Stage<T> S, co
         v = qr * (S.s[e - px - 1] + S.s[e - px] + S.s[e - 1] + S.s[e]) * S.Ts[0][e];
       S.sns[0][e] = v;
       if (check) {
-        sig = fabs((double)v);
+        sig = (T)fabs(v);
         if (S.relax) {
-          dtau = fabs((double)v - (double)S.cs[0][e]);
+          dtau = (T)fabs(v - S.cs[0][e]);
           S.cs[0][e] = v;
         }
       }
@@ -312,10 +317,9 @@ __global__ void __launch_bounds__(kThreads) k_return_edges(Geo g, Stage<T> S, co
       S.sns[1][e] = v1;
       S.sns[2][e] = v2;
       if (check) {
-        sig = maxn(fabs((double)v0), maxn(fabs((double)v1), fabs((double)v2)));
+        sig = maxt((T)fabs(v0), maxt((T)fabs(v1), (T)fabs(v2)));
         if (S.relax) {
-          dtau = maxn(fabs((double)v0 - (double)S.cs[0][e]),
-                      maxn(fabs((double)v1 - (double)S.cs[1][e]), fabs((double)v2 - (double)S.cs[2][e])));
+          dtau = maxt((T)fabs(v0 - S.cs[0][e]), maxt((T)fabs(v1 - S.cs[1][e]), (T)fabs(v2 - S.cs[2][e])));
           S.cs[0][e] = v0;
           S.cs[1][e] = v1;
           S.cs[2][e] = v2;
@@ -324,8 +328,8 @@ __global__ void __launch_bounds__(kThreads) k_return_edges(Geo g, Stage<T> S, co
     }
   }
   if (check && di) {
-    block_max(abs_bits(sig), &di->red[RED_SIG]);
-    block_max(abs_bits(dtau), &di->red[RED_DTAU]);
+    block_max(abs_bits((double)sig), &di->red[RED_SIG]);
+    block_max(abs_bits((double)dtau), &di->red[RED_DTAU]);
   }
 }
 
@@ -338,7 +342,8 @@ __global__ void __launch_bounds__(kThreads) k_velocity(Geo g, Stage<T> S, const 
   const int i = q.i, j = q.j, k = q.k, nx = g.nx, ny = g.ny, nz = g.nz;
   const long long e = q.e, px = g.px, pl = g.plane;
   const T rdx = (T)g.rdx, rdy = (T)g.rdy, rdz = (T)g.rdz, vs = (T)sc->vstep;
-  double rmax = 0.0, du = 0.0, vm = 0.0;
+  T rmax = 0, du = 0;
+  double vm = 0.0;   // |v0 + u| needs the FP64 base velocity
   if (q.in && i <= nx && j <= ny && k <= (ND == 3 ? nz : 0)) {
     // x-faces: i <= nx, j < ny, k < nz
     if (j < ny && (ND == 2 || k < nz)) {
@@ -349,11 +354,11 @@ __global__ void __launch_bounds__(kThreads) k_velocity(Geo g, Stage<T> S, const 
         if (ND == 3) R += (S.sns[1][e + pl] - S.sns[1][e]) * rdz;
         if (S.f[0]) R += S.f[0][e];
         un = u + vs * R;
-        if (check) rmax = fabs((double)R);
+        if (check) rmax = (T)fabs(R);
       }
       S.uo[0][e] = un;
       if (check) {
-        du = fabs((double)un - (double)S.uchk[0][e]);
+        du = (T)fabs(un - S.uchk[0][e]);
         vm = fabs(S.v0[0][e] + (double)u);
         S.uchk[0][e] = un;
       }
@@ -369,11 +374,11 @@ __global__ void __launch_bounds__(kThreads) k_velocity(Geo g, Stage<T> S, const 
         if (ND == 3) R += (S.sns[2][e + pl] - S.sns[2][e]) * rdz;
         if (S.f[1]) R += S.f[1][e];
         un = u + vs * R;
-        if (check) rmax = maxn(rmax, fabs((double)R));
+        if (check) rmax = maxt(rmax, (T)fabs(R));
       }
       S.uo[1][e] = un;
       if (check) {
-        du = maxn(du, fabs((double)un - (double)S.uchk[1][e]));
+        du = maxt(du, (T)fabs(un - S.uchk[1][e]));
         vm = maxn(vm, fabs(S.v0[1][e] + (double)u));
         S.uchk[1][e] = un;
       }
@@ -389,11 +394,11 @@ __global__ void __launch_bounds__(kThreads) k_velocity(Geo g, Stage<T> S, const 
                 (S.sns[1][e + 1] - S.sns[1][e]) * rdx + (S.sns[2][e + px] - S.sns[2][e]) * rdy;
           if (S.f[2]) R += S.f[2][e];
           un = u + vs * R;
-          if (check) rmax = maxn(rmax, fabs((double)R));
+          if (check) rmax = maxt(rmax, (T)fabs(R));
         }
         S.uo[2][e] = un;
         if (check) {
-          du = maxn(du, fabs((double)un - (double)S.uchk[2][e]));
+          du = maxt(du, (T)fabs(un - S.uchk[2][e]));
           vm = maxn(vm, fabs(S.v0[2][e] + (double)u));
           S.uchk[2][e] = un;
         }
@@ -403,8 +408,8 @@ __global__ void __launch_bounds__(kThreads) k_velocity(Geo g, Stage<T> S, const 
     }
   }
   if (check && di) {
-    block_max(abs_bits(rmax), &di->red[RED_R]);
-    block_max(abs_bits(du), &di->red[RED_DU]);
+    block_max(abs_bits((double)rmax), &di->red[RED_R]);
+    block_max(abs_bits((double)du), &di->red[RED_DU]);
     block_max(abs_bits(vm), &di->red[RED_V]);
   }
 }
