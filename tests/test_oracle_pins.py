@@ -695,3 +695,42 @@ def test_golden_closed_forms_against_the_oracle():
         if first is None and o.get("epl").max() > 0:
             first = inc
     assert first == int(gd["maxwell_first_plastic_increment"])
+
+
+# ---------------------------------------------------------------- P8 ------
+def _anomaly_run(ndim, n, jaumann, incs=2, **solver):
+    """Elastic box seeded by an initial pressure anomaly (out of equilibrium,
+    so the increments iterate), solved to tol 1e-13."""
+    L = (2.0, 1.0, 1.0)[:ndim]
+    s = E.Setup("p8", ndim, n, L=L + (1.0,) * (3 - ndim), mu_s=1e6, c0=1.0, inclusion_radius=0.0, noise=0.0,
+                tol=1e-13, load_plane="xz" if ndim == 3 else "xy")
+    o = O.from_setup(s, jaumann=jaumann, n_chk=10, **solver)
+    o.set("p", E.pressure_anomaly(n, L, 1e-3, 0.2))
+    rates = [1.0, -1.0] if ndim == 2 else [1.0, 0.0, -1.0]
+    fields = ["txx", "tyy", "txy", "p", "vx", "vy"] + (["tzz", "txz", "tyz", "vz"] if ndim == 3 else [])
+    out = []
+    for _ in range(incs):
+        o.apply_increment(rates, s.dt)
+        info = o.solve_increment()
+        out.append((info["iters"], {f: o.get(f).copy() for f in fields}))
+    return out
+
+
+@pytest.mark.parametrize("ndim,n,jaumann", [(2, (32, 16), False), (2, (32, 16), True), (3, (12, 8, 7), True)])
+def test_p8_elastic_fixed_point_is_independent_of_pt_parameters(ndim, n, jaumann):
+    """The converged elastic increment is the solution of R(v) = 0 and must
+    not depend on the pseudo-transient parameters (C_cfl x 0.7, Re x 0.5 and
+    x 2 change the iteration counts, not the answer).  In plastic increments
+    the fixed point does depend on them (vertex/edge scales are means of the
+    centre scales of relaxed trials), so this pin stays elastic."""
+    base = _anomaly_run(ndim, n, jaumann)
+    assert base[0][0] > 0
+    for kw in (dict(c_cfl=0.7 * 0.9 / math.sqrt(ndim)), dict(xi=0.5), dict(xi=2.0)):
+        other = _anomaly_run(ndim, n, jaumann, **kw)
+        assert any(a[0] != b[0] for a, b in zip(base, other)), kw
+        for (_, fa), (_, fb) in zip(base, other):
+            vscale = max(np.abs(fa[f]).max() for f in fa if f.startswith("v"))
+            sscale = max(np.abs(fa[f]).max() for f in fa if not f.startswith("v"))
+            for f in fa:
+                scale = vscale if f.startswith("v") else sscale
+                assert np.abs(fa[f] - fb[f]).max() <= 1e-11 * scale, (kw, f)
