@@ -71,6 +71,7 @@ def lib():
         L.or_set_solver.argtypes = [P, D, Lg, I, D, D, D, I]
         L.or_set_freeze.argtypes = [P, Lg, D]
         L.or_set_advection.argtypes = [P, I]
+        L.or_set_incompressible.argtypes = [P, I]
         L.or_advect.argtypes = [P, D]
         L.or_apply_increment.argtypes = [P, DP, D, DP]
         L.or_solve_increment.argtypes = [P, C.POINTER(Info)]
@@ -138,12 +139,13 @@ class Oracle:
         self._chk(self.L_.or_set_material(self.h, K, G, mu_s, phi_deg, psi_deg, _dp(c)), "set_material")
 
     def set_solver(self, tol=1e-8, max_iter=1000000, n_chk=100, c_cfl=None, xi=1.0, r_pt=0.5,
-                   jaumann=True, advection=False):
+                   jaumann=True, advection=False, incompressible=False):
         if c_cfl is None:
             c_cfl = 0.9 / math.sqrt(self.ndim)
         self._chk(self.L_.or_set_solver(self.h, tol, int(max_iter), int(n_chk), c_cfl, xi, r_pt,
                                         int(jaumann)), "set_solver")
         self._chk(self.L_.or_set_advection(self.h, int(bool(advection))), "set_advection")
+        self._chk(self.L_.or_set_incompressible(self.h, int(bool(incompressible))), "set_incompressible")
 
     def advect(self, dt):
         """Advect the old stress (tau_hat, p_hat) over dt with the velocity

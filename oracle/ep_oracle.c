@@ -40,6 +40,10 @@
  *    discretisation): once per increment, explicit first-order upwind
  *    transport of the history deviator and pressure over dt with the
  *    previous increment's converged velocity (see advect_history);
+ *  - optional incompressible variant (Eq. A2ssP2 in place of Eq. A2ssP): the
+ *    pressure is pseudo-time state stepped by -K~ div v, starts at p_hat, and
+ *    its stopping measure is 2 eta_ve times the interval-averaged divergence
+ *    (see or_set_incompressible);
  *  - each iteration starts from the stress consistent with the start
  *    velocity (one pseudo step with no relaxation memory);
  *  - the stopping test takes the largest of the three equations' residuals,
@@ -95,6 +99,8 @@ typedef struct {
   int frozen;
   /* advection of the old stress (Eq. j1), once per committed increment */
   int advect;
+  /* incompressible pressure equation (Eq. A2ssP2) instead of Eq. A2ssP */
+  int incompressible;
   long commits, adv_done;
   /* loading of the current increment (Eqs. A7-A9M) */
   double rate[3], dt;
@@ -457,9 +463,19 @@ static pt_t pt_params(const or_grid *g) {
 static void pt_stress(or_grid *g, double bt, double bp) {
   const int nx = g->nx, ny = g->ny, nz = g->nz;
   long nc = n_centres(g);
-  /* pressure, Eq. A2ssP: p = bp p_k + (1 - bp) (p_hat - K dt div v) */
-  for (long c = 0; c < nc; ++c)
-    g->pc[c] = bp * g->p_k[c] + (1.0 - bp) * (g->p[c] - g->K * g->dt * g->div[c]);
+  if (!g->incompressible) {
+    /* pressure, Eq. A2ssP: p = bp p_k + (1 - bp) (p_hat - K dt div v) */
+    for (long c = 0; c < nc; ++c)
+      g->pc[c] = bp * g->p_k[c] + (1.0 - bp) * (g->p[c] - g->K * g->dt * g->div[c]);
+  } else if (bt != 0.0 || bp != 0.0) {
+    /* pressure, Eq. A2ssP2 with pseudo step 1: p = p_k - K~ div v */
+    const double Kt = pt_params(g).Kt;
+    for (long c = 0; c < nc; ++c) g->pc[c] = g->p_k[c] - Kt * g->div[c];
+  } else {
+    /* the physical response: the pressure is no function of v here, it
+     * keeps its old value */
+    memcpy(g->pc, g->p, sizeof(double) * nc);
+  }
   /* relaxed trial deviator, Eq. A23ssP: T = bt tau_k + (1 - bt) tau_tr */
   for (long c = 0; c < nc; ++c)
     for (int d = 0; d < g->ndim; ++d) g->Tn[d][c] = bt * g->tn_k[d][c] + (1.0 - bt) * g->trn[d][c];
@@ -655,6 +671,16 @@ static int advect_history(or_grid *g, double dt) {
   return OR_OK;
 }
 
+/* Incompressible variant (Sec. 3.2, Eq. A2ssP2): the pressure equation
+ * (1/K~) dp/dt~ = -div v replaces Eq. A2ssP; K is not used.  The pressure is
+ * pseudo-time state that starts at p_hat (no function of v gives it), and
+ * its stopping measure is 2 eta_ve <|div v|> / max|sigma|: the volumetric
+ * rate error in the stress units of the deviatoric response. */
+int or_set_incompressible(or_grid *g, int on) {
+  g->incompressible = on != 0;
+  return OR_OK;
+}
+
 /* Switch the per-increment advection of the old stress on or off. */
 int or_set_advection(or_grid *g, int on) {
   g->advect = on != 0;
@@ -847,7 +873,13 @@ int or_solve_increment(or_grid *g, or_info *info) {
       }
       double em = (dvm == 0.0) ? 0.0 : (ms > 0.0 ? dxm * dvm / (m * q.vstep) / ms : INFINITY);
       double et = (dtau == 0.0) ? 0.0 : (ms > 0.0 ? dtau / (m * (1.0 - q.beta_tau)) / ms : INFINITY);
-      double ep = (dp == 0.0) ? 0.0 : (ms > 0.0 ? dp / (m * (1.0 - q.beta_p)) / ms : INFINITY);
+      /* pressure measure: the distance of p from its target (compressible);
+       * incompressible, 2 eta_ve times the interval-averaged divergence
+       * (p_{k+1} - p_chk = -K~ m <div v>) */
+      double ep = (dp == 0.0) ? 0.0
+                  : !(ms > 0.0) ? INFINITY
+                  : g->incompressible ? 2.0 * eta_ve(g) * dp / (m * q.Kt) / ms
+                                      : dp / (m * (1.0 - q.beta_p)) / ms;
       double er = em > et ? em : et;
       if (ep > er) er = ep;
       info->iters = k; info->eps_res = er; info->eps_mom = em; info->eps_tau = et; info->eps_p = ep;
