@@ -97,7 +97,10 @@ typedef struct {
    * after a committed one first transports tau_hat and p_hat over its dt with
    * the last converged velocity (explicit first-order upwind; zero gradient
    * at inflow walls; free-slip wall shear stays zero).  Stable for
-   * max|v| dt / dx_min <= 1 / ndim.  Default 0 (off). */
+   * max|v| dt / dx_min <= 1 / ndim.  The count of committed increments
+   * decides: a grid resumed through ep_set_fields advects from its first
+   * commit on, and ep_restore brings back the state before the advection of
+   * the checkpointed increment.  Default 0 (off). */
   int advection;
 } ep_solver_opts;
 

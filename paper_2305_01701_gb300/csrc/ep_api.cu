@@ -72,7 +72,7 @@ struct ep_grid {
   unsigned long long *wscale = nullptr;
   char *snap = nullptr;     // checkpoint of the history (ep_snapshot)
   bool snap_started = false;
-  int snap_commits = 0;
+  int snap_commits = 0, snap_adv_done = 0;
   std::string err;
 };
 
@@ -1003,6 +1003,7 @@ ep_status ep_snapshot(ep_handle h) {
   CK(h, cudaStreamSynchronize(h->stream));
   h->snap_started = h->started;
   h->snap_commits = h->n_commits;
+  h->snap_adv_done = h->adv_done;
   return EP_OK;
 }
 
@@ -1016,6 +1017,7 @@ ep_status ep_restore(ep_handle h) {
   CK(h, cudaStreamSynchronize(h->stream));
   h->started = h->snap_started;
   h->n_commits = h->snap_commits;
+  h->adv_done = h->snap_adv_done;   // a restored history is advected again
   h->in_increment = false;
   return EP_OK;
 }
@@ -1432,6 +1434,8 @@ ep_status ep_destroy(ep_handle h) {
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   if (h->own_arena && h->arena) cudaFree(h->arena);
   if (h->snap) cudaFree(h->snap);
+  if (h->wx) cudaFree(h->wx);   // warm-start network input / output
+  if (h->wy) cudaFree(h->wy);
   delete h;
   return EP_OK;
 }

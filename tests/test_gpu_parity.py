@@ -267,6 +267,28 @@ def test_advection_fp64_parity_2d(P):
     g.close()
 
 
+def test_advection_survives_snapshot_and_restore(P):
+    """An increment solved, restored from the checkpoint taken before it and
+    solved again advects the restored history again: same iterations, same
+    fields bit for bit."""
+    s = E.config(1, n=(32, 28), tol=1e-9)
+    g = gpu_grid(P, s, P.FP64, advection=True)
+    for _ in range(6):
+        g.apply_increment_rates(rates_of(s), s.dt)
+        g.solve_increment()
+    g.snapshot()
+    g.apply_increment_rates(rates_of(s), s.dt)
+    i1 = g.solve_increment()
+    f1 = {f: g.get(f) for f in FIELDS_2D}
+    g.restore()
+    g.apply_increment_rates(rates_of(s), s.dt)
+    i2 = g.solve_increment()
+    assert i1["iters"] == i2["iters"]
+    for f in FIELDS_2D:
+        np.testing.assert_array_equal(g.get(f), f1[f], err_msg=f)
+    g.close()
+
+
 @pytest.mark.parametrize("variant", [0, 3])
 def test_advection_fp64_parity_3d(P, variant):
     """Advection on in 3D (x-z pure shear) with the staged and the register
