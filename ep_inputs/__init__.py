@@ -99,8 +99,15 @@ class Setup:
     extra: dict = field(default_factory=dict)
 
     def cohesion(self) -> np.ndarray:
+        if "cohesion" in self.extra:
+            return self.extra["cohesion"].copy()
         return cohesion_field(self.n, self.L[: self.ndim], self.c0, self.noise, self.seed,
                               self.inclusion_radius, self.inclusion_centre[: self.ndim])
+
+    def shear_modulus(self):
+        """The per-cell shear modulus of the setup, or None (uniform G)."""
+        g = self.extra.get("shear_modulus")
+        return None if g is None else g.copy()
 
     def initial_pressure(self):
         """The initial (history) pressure of the setup, or None (zero)."""
@@ -192,3 +199,44 @@ def batch_setups(count: int = 256, base_seed: int = 4000, sizes=BATCH_SIZES) -> 
                   tol=1e-6, precision="fp32")
         out.append(s)
     return out
+
+
+def gaussian_fields(n, L, G0=1.0, c0=2e-3, width=0.2, wall_band=0.05):
+    """The paper's heterogeneous setup (Sec. 4.1): a shear modulus rising as a
+    Gaussian from G0 at the centre to 1.2 G0 at the walls,
+        G = G0 (1.2 - 0.2 exp(-(r / w)^2)),
+    and a cohesion rising the same way from c0 at the centre towards 1.5 c0,
+        c = c0 (1.5 - 0.5 exp(-(r / w)^2)),
+    with a jump to 2 c0 within ``wall_band`` of any wall; r is the distance of
+    the cell centre from the box centre, w = ``width`` times the shortest box
+    side.  Shapes as :func:`cohesion_field`."""
+    ndim = len(n)
+    axes = cell_centres(n, L)
+    grids = np.meshgrid(*reversed(axes), indexing="ij")
+    r2 = np.zeros(tuple(reversed(n)))
+    near_wall = np.zeros(tuple(reversed(n)), dtype=bool)
+    for d in range(ndim):
+        xd = grids[ndim - 1 - d]
+        r2 += xd ** 2
+        near_wall |= np.abs(xd) >= 0.5 * L[d] - wall_band * min(L)
+    w = width * min(L)
+    bump = np.exp(-r2 / w ** 2)
+    G = G0 * (1.2 - 0.2 * bump)
+    c = np.where(near_wall, 2.0 * c0, c0 * (1.5 - 0.5 * bump))
+    return np.ascontiguousarray(G), np.ascontiguousarray(c)
+
+
+def gaussian_setup(ndim=2, n=None, **overrides) -> Setup:
+    """The box of the paper's heterogeneous runs (Sec. 4.1; Sec. 4.4 uses it
+    at 511^2): Gaussian G-bar (1 at the centre, 1.2 at the walls) and c-bar
+    (0.2e-2 at the centre, a jump to 0.4e-2 near the walls), phi = 30 deg,
+    zero initial stress.  The paper prints neither the Gaussian's width nor
+    the band of the jump; :func:`gaussian_fields` fixes both."""
+    n = tuple(n) if n is not None else ((511, 511) if ndim == 2 else (127, 127, 127))
+    s = Setup("%dd-gaussian" % ndim, ndim, n, c0=2e-3, inclusion_radius=0.0, noise=0.0, seed=7000,
+              load_plane="xy" if ndim == 2 else "xz", increments=30, tol=1e-8)
+    G, c = gaussian_fields(n, (1.0,) * ndim)
+    s.extra = {"shear_modulus": G, "cohesion": c}
+    for k, v in overrides.items():
+        setattr(s, k, v)
+    return s

@@ -72,6 +72,7 @@ def lib():
         L.or_set_freeze.argtypes = [P, Lg, D]
         L.or_set_advection.argtypes = [P, I]
         L.or_set_incompressible.argtypes = [P, I]
+        L.or_set_shear_modulus.argtypes = [P, DP]
         L.or_advect.argtypes = [P, D]
         L.or_apply_increment.argtypes = [P, DP, D, DP]
         L.or_solve_increment.argtypes = [P, C.POINTER(Info)]
@@ -146,6 +147,14 @@ class Oracle:
                                         int(jaumann)), "set_solver")
         self._chk(self.L_.or_set_advection(self.h, int(bool(advection))), "set_advection")
         self._chk(self.L_.or_set_incompressible(self.h, int(bool(incompressible))), "set_incompressible")
+
+    def set_shear_modulus(self, Gc):
+        """Per-cell shear modulus (one value per centre), or None for the
+        uniform G of set_material."""
+        a = None if Gc is None else np.ascontiguousarray(Gc, dtype=np.float64).ravel()
+        if a is not None and a.size != int(np.prod(self.n)):
+            raise ValueError("set_shear_modulus: one value per cell centre")
+        self._chk(self.L_.or_set_shear_modulus(self.h, _dp(a) if a is not None else None), "set_shear_modulus")
 
     def advect(self, dt):
         """Advect the old stress (tau_hat, p_hat) over dt with the velocity

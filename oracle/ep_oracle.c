@@ -44,6 +44,11 @@
  *    pressure is pseudo-time state stepped by -K~ div v, starts at p_hat, and
  *    its stopping measure is 2 eta_ve times the interval-averaged divergence
  *    (see or_set_incompressible);
+ *  - optional per-cell shear modulus (the paper's Gaussian G-bar, Sec. 4.1):
+ *    eta_ve and the weight of the rotated old stress follow G point by point,
+ *    a vertex/edge takes the arithmetic mean of its adjacent centres' G, and
+ *    the pseudo-transient parameters use the largest G (see
+ *    or_set_shear_modulus);
  *  - each iteration starts from the stress consistent with the start
  *    velocity (one pseudo step with no relaxation memory);
  *  - the stopping test takes the largest of the three equations' residuals,
@@ -87,6 +92,8 @@ typedef struct {
   /* material (Eqs. A43, A61, A611, A6121) */
   double K, G, mu_s, A, B;
   double *coh;
+  double *Gc;     /* per-centre shear modulus (NULL: the uniform G) */
+  double Gref;    /* its largest value, for the pseudo-transient parameters */
   int have_material;
   /* solver settings */
   double tol, c_cfl, xi, r_pt;
@@ -192,6 +199,7 @@ or_grid *or_create(int ndim, const int *n, const double *L) {
 
 void or_destroy(or_grid *g) {
   if (!g) return;
+  free(g->Gc);
   free(g->coh); free(g->p); free(g->epl); free(g->div); free(g->pc); free(g->s); free(g->p_k); free(g->p_c);
   for (int d = 0; d < 3; ++d) {
     free(g->v[d]); free(g->u[d]); free(g->v0[d]); free(g->vi[d]); free(g->vchk[d]);
@@ -254,8 +262,32 @@ static int is_boundary_face(const or_grid *g, int d, int i, int j, int k) {
 
 /* viscoelastic effective viscosity eta_ve = (1/(G dt) + 1/mu_s)^-1, the
  * coefficient of Eq. A23ssP at pseudo-steady state; mu_s = inf gives G dt. */
-static double eta_ve(const or_grid *g) {
-  return isinf(g->mu_s) ? g->G * g->dt : 1.0 / (1.0 / (g->G * g->dt) + 1.0 / g->mu_s);
+static double eta_for(const or_grid *g, double G) {
+  return isinf(g->mu_s) ? G * g->dt : 1.0 / (1.0 / (G * g->dt) + 1.0 / g->mu_s);
+}
+/* the viscosity the pseudo-transient parameters use (the largest G) */
+static double eta_ve(const or_grid *g) { return eta_for(g, g->Gc ? g->Gref : g->G); }
+/* shear modulus at a centre */
+static double G_centre(const or_grid *g, long c) { return g->Gc ? g->Gc[c] : g->G; }
+/* shear modulus at point (i, j, k) of shear component s (2D vertices, 3D
+ * edges): the mean over the centres around it (one layer in each dimension
+ * where the point sits at cell centres, two where it sits on grid lines;
+ * indices clamped at the walls, whose shear stress is zero anyway) */
+static double G_shear(const or_grid *g, int s, int i, int j, int k) {
+  if (!g->Gc) return g->G;
+  const int st[3] = {g->ndim == 2 ? 1 : s != 2, g->ndim == 2 ? 1 : s != 1, g->ndim == 2 ? 0 : s != 0};
+  const int q[3] = {i, j, k}, n[3] = {g->nx, g->ny, g->nz};
+  double sum = 0.0;
+  int cnt = 0;
+  for (int c = -st[2]; c <= 0; ++c)
+    for (int b = -st[1]; b <= 0; ++b)
+      for (int a = -st[0]; a <= 0; ++a) {
+        int idx[3] = {q[0] + a, q[1] + b, q[2] + c};
+        for (int d = 0; d < 3; ++d) idx[d] = idx[d] < 0 ? 0 : idx[d] > n[d] - 1 ? n[d] - 1 : idx[d];
+        sum += g->Gc[CI(idx[0], idx[1], idx[2])];
+        ++cnt;
+      }
+  return sum / cnt;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -413,14 +445,19 @@ static void rotated_history_3d(or_grid *g) {
 /* plastic term.  Walls carry zero.                                          */
 /* ------------------------------------------------------------------------ */
 static void trial(or_grid *g) {
-  const double eta = eta_ve(g), c2 = eta / (g->G * g->dt);
   long nc = n_centres(g);
-  for (long c = 0; c < nc; ++c)
+  for (long c = 0; c < nc; ++c) {
+    const double G = G_centre(g, c), eta = eta_for(g, G), c2 = eta / (G * g->dt);
     for (int d = 0; d < g->ndim; ++d)
       g->trn[d][c] = 2.0 * eta * (g->en[d][c] - g->div[c] / 3.0) + c2 * g->tJn[d][c];
+  }
   for (int s = 0; s < n_shear_comp(g); ++s) {
-    long ns = n_shear(g, s);
-    for (long e = 0; e < ns; ++e) g->trs[s][e] = 2.0 * eta * g->es[s][e] + c2 * g->tJs[s][e];
+    int ex, ey, ez; shear_dims(g, s, &ex, &ey, &ez);
+    for (int k = 0; k < ez; ++k) for (int j = 0; j < ey; ++j) for (int i = 0; i < ex; ++i) {
+      const long e = ((long)k * ey + j) * ex + i;
+      const double G = G_shear(g, s, i, j, k), eta = eta_for(g, G), c2 = eta / (G * g->dt);
+      g->trs[s][e] = 2.0 * eta * g->es[s][e] + c2 * g->tJs[s][e];
+    }
   }
 }
 
@@ -681,6 +718,26 @@ int or_set_incompressible(or_grid *g, int on) {
   return OR_OK;
 }
 
+/* Per-cell shear modulus (one positive value per centre, copied; NULL
+ * returns to the uniform G of or_set_material).  eta_ve and the weight of
+ * the rotated old stress then vary point by point (vertices/edges: mean of
+ * the adjacent centres); the pseudo-transient parameters use the largest G,
+ * which changes the iteration count but not the fixed point. */
+int or_set_shear_modulus(or_grid *g, const double *Gc) {
+  if (!Gc) { free(g->Gc); g->Gc = NULL; return OR_OK; }
+  const long nc = n_centres(g);
+  double mx = 0.0;
+  for (long c = 0; c < nc; ++c) {
+    if (!(Gc[c] > 0.0) || isinf(Gc[c])) return OR_ERR_ARG;
+    if (Gc[c] > mx) mx = Gc[c];
+  }
+  if (!g->Gc) g->Gc = zalloc(nc);
+  if (!g->Gc) return OR_ERR_OOM;
+  memcpy(g->Gc, Gc, sizeof(double) * nc);
+  g->Gref = mx;
+  return OR_OK;
+}
+
 /* Switch the per-increment advection of the old stress on or off. */
 int or_set_advection(or_grid *g, int on) {
   g->advect = on != 0;
@@ -933,7 +990,7 @@ int or_eval(or_grid *g, const double *v, double *max_r, double *max_sig) {
  * converged velocity becomes the iterate. */
 int or_commit(or_grid *g) {
   if (!g->in_increment || !g->evaluated) return OR_ERR_STATE;
-  const double dt = g->dt, eta = eta_ve(g);
+  const double dt = g->dt;
   const int nx = g->nx, ny = g->ny, nz = g->nz;
   for (int k = 0; k < nz; ++k) for (int j = 0; j < ny; ++j) for (int i = 0; i < nx; ++i) {
     long c = CI(i, j, k);
@@ -949,7 +1006,7 @@ int or_commit(or_grid *g) {
                           (g->trs[2][YZI(i, j, k + 1)] - g->ss[2][YZI(i, j, k + 1)]) + (g->trs[2][YZI(i, j + 1, k + 1)] - g->ss[2][YZI(i, j + 1, k + 1)]));
       J2 += b * b + cc * cc;
     }
-    if (g->s[c] < 1.0) g->epl[c] += dt * sqrt(J2) / (2.0 * eta);   /* only where the return acted */
+    if (g->s[c] < 1.0) g->epl[c] += dt * sqrt(J2) / (2.0 * eta_for(g, G_centre(g, c)));   /* only where the return acted */
   }
   long nc = n_centres(g);
   for (long c = 0; c < nc; ++c) {

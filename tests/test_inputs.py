@@ -7,6 +7,7 @@ OOPSLA 2014; the reference implementation's sequences for seeds 0 and
 import math
 
 import numpy as np
+import pytest
 
 import ep_inputs as E
 
@@ -57,3 +58,19 @@ def test_pressure_anomaly_by_brute_force():
     assert (big > 0).sum() == sum(1 for j in range(191) for i in range(383)
                                   if (-1.0 + (i + 0.5) * 2 / 383) ** 2 + (-0.5 + (j + 0.5) / 191) ** 2 <= 0.0025)
     assert math.isclose(big.max(), 1e-3)
+
+
+def test_gaussian_fields_by_brute_force():
+    n, L = (12, 11), (1.0, 1.0)          # no cell centre on the edge of the wall band
+    G, c = E.gaussian_fields(n, L)
+    w = 0.2
+    for j in range(n[1]):
+        for i in range(n[0]):
+            x, y = -0.5 + (i + 0.5) / n[0], -0.5 + (j + 0.5) / n[1]
+            bump = math.exp(-(x * x + y * y) / w ** 2)
+            assert G[j, i] == pytest.approx(1.0 * (1.2 - 0.2 * bump), rel=1e-14)
+            wall = abs(x) >= 0.45 or abs(y) >= 0.45
+            assert c[j, i] == pytest.approx(4e-3 if wall else 2e-3 * (1.5 - 0.5 * bump), rel=1e-14)
+    s = E.gaussian_setup(n=(16, 16))
+    assert s.shear_modulus().shape == (16, 16) and s.cohesion().shape == (16, 16)
+    assert s.shear_modulus().min() > 1.0 and s.shear_modulus().max() < 1.2
