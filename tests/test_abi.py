@@ -92,3 +92,19 @@ def test_binding_structs_match_the_header_layout(cls, struct):
     size, offs = _c_layout(struct, names)
     assert ctypes.sizeof(S) == size
     assert [getattr(S, n).offset for n in names] == offs
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """No CPU fallback: without libep.so the binding raises instead of
+    computing anything."""
+    from paper_2305_01701_gb300 import _native
+    saved_path, saved_lib = _native.LIB_PATH, _native._lib
+    try:
+        _native.LIB_PATH = str(tmp_path / "libep.so")
+        _native._lib = None
+        with pytest.raises(ImportError):
+            _native.lib()
+        with pytest.raises(ImportError):
+            _native.Grid(2, (8, 8))
+    finally:
+        _native.LIB_PATH, _native._lib = saved_path, saved_lib
