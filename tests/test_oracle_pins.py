@@ -734,3 +734,29 @@ def test_p8_elastic_fixed_point_is_independent_of_pt_parameters(ndim, n, jaumann
             for f in fa:
                 scale = vscale if f.startswith("v") else sscale
                 assert np.abs(fa[f] - fb[f]).max() <= 1e-11 * scale, (kw, f)
+
+
+# ------------------------------------------- line integrals by equilibrium --
+def test_line_integrals_of_sigma_xx_agree_by_equilibrium_2d():
+    """2D equilibrium d(sigma_xx)/dx + d(sigma_xy)/dy = 0 with zero shear
+    stress on the free-slip walls makes the integral of sigma_xx over every
+    vertical line the same (the discrete momentum balance telescopes the same
+    way over a column of x-faces).  So at convergence the centre-column and
+    right-column integrals (G15) agree, through yield and localization, for
+    heterogeneous, visco-elastic and pressure-seeded boxes."""
+    import ep_inputs as E
+    cases = [(E.config(1, n=(40, 36), tol=1e-12), {}, None),
+             (E.config(1, n=(30, 30), tol=1e-12, mu_s=2e-3), {}, None),
+             (E.anomaly_setup(n=(48, 24), tol=1e-12), {"jaumann": False}, "p")]
+    for s, kw, seed in cases:
+        o = O.from_setup(s, **kw)
+        if seed:
+            o.set("p", s.initial_pressure())
+        plastic = 0
+        for _ in range(9):
+            o.apply_increment([1.0, -1.0], s.dt)
+            info = o.solve_increment()
+            plastic += info["n_plastic"] > 0
+            a, b = info["sxx_int_centre"], info["sxx_int_right"]
+            assert abs(a - b) <= 1e-10 * abs(a), (s.name, a, b)
+        assert plastic > 0
