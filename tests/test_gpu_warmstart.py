@@ -68,6 +68,40 @@ def test_net_forward_and_gradient_match_oracle(P, nd, shape, base, levels):
     net.close()
 
 
+def test_features_and_targets_match_their_numpy_definition(P):
+    """The feature and target kernels against their plain numpy definition
+    (oracle/warm_oracle.py) on a 2D FP64 grid past first yield (so the scale
+    channel varies): the scale S exactly, every channel within FP32
+    rounding."""
+    import torch
+    from oracle import warm_oracle as WO
+    s = E.config(1, n=(30, 26), tol=1e-9)
+    g = P.Grid(2, s.n, precision=P.FP64)
+    g.set_material(s.K, s.G, s.mu_s, s.phi_deg, s.psi_deg, s.cohesion())
+    g.set_solver(tol=s.tol)
+    vs = []
+    for _ in range(7):
+        g.apply_increment(1.0, s.dt, P.LOAD_XY)
+        g.solve_increment()
+        vs.append([g.get("vx"), g.get("vy")])
+    assert (g.get("scale") < 1).any()
+    nv = int(np.prod(g.warm_dims()))
+    x = torch.zeros(4 * nv, dtype=torch.float32, device="cuda")
+    S = g.warm_features(x.data_ptr())
+    torch.cuda.synchronize()
+    f_np, S_np = WO.features(s.n, vs[-1], vs[-2], g.get("scale"), s.cohesion())
+    assert S == S_np
+    f_gpu = x.cpu().numpy()
+    np.testing.assert_allclose(f_gpu, f_np, rtol=1e-6, atol=1e-7)
+    g.apply_increment(1.0, s.dt, P.LOAD_XY)
+    g.solve_increment()
+    t = torch.zeros(2 * nv, dtype=torch.float32, device="cuda")
+    g.warm_target(x.data_ptr(), S, t.data_ptr())
+    t_np = WO.target(s.n, [g.get("vx"), g.get("vy")], vs[-1], S, f_gpu)
+    np.testing.assert_allclose(t.cpu().numpy(), t_np, rtol=1e-5, atol=1e-6)
+    g.close()
+
+
 def test_training_reduces_the_loss(P):
     import torch
     rng = np.random.default_rng(0)
