@@ -34,6 +34,7 @@ class Samples:
         self.nv = nv
         self.x = torch.zeros((capacity, ndim + 2, nv), dtype=torch.float32, device=device)
         self.t = torch.zeros((capacity, ndim, nv), dtype=torch.float32, device=device)
+        torch.cuda.synchronize()   # zeroed before the library writes on its own stream
         self.n = 0
 
     def ptr_x(self, i):

@@ -87,6 +87,7 @@ def test_features_and_targets_match_their_numpy_definition(P):
     assert (g.get("scale") < 1).any()
     nv = int(np.prod(g.warm_dims()))
     x = torch.zeros(4 * nv, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()   # the library writes on its own (non-blocking) stream
     S = g.warm_features(x.data_ptr())
     torch.cuda.synchronize()
     f_np, S_np = WO.features(s.n, vs[-1], vs[-2], g.get("scale"), s.cohesion())
@@ -96,6 +97,7 @@ def test_features_and_targets_match_their_numpy_definition(P):
     g.apply_increment(1.0, s.dt, P.LOAD_XY)
     g.solve_increment()
     t = torch.zeros(2 * nv, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
     g.warm_target(x.data_ptr(), S, t.data_ptr())
     t_np = WO.target(s.n, [g.get("vx"), g.get("vy")], vs[-1], S, f_gpu)
     np.testing.assert_allclose(t.cpu().numpy(), t_np, rtol=1e-5, atol=1e-6)
