@@ -57,35 +57,66 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
-def lib():
+def build_variant(source: str, tag: str) -> str:
+    """Compile a modified copy of the oracle's source (a test that plants a
+    mistake in the oracle to show that a pin catches it) into
+    ``oracle/lib/variant_<tag>.so``; returns its path."""
+    os.makedirs(_LIBDIR, exist_ok=True)
+    src = os.path.join(_LIBDIR, "variant_%s_%d.c" % (tag, os.getpid()))
+    out = os.path.join(_LIBDIR, "variant_%s_%d.so" % (tag, os.getpid()))
+    with open(src, "w") as f:
+        f.write(source)
+    subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-D_GNU_SOURCE", "-ffp-contract=off",
+                    "-o", out, src, "-lm"], check=True)
+    os.remove(src)
+    return out
+
+
+def source() -> str:
+    with open(_SRC) as f:
+        return f.read()
+
+
+_variants = {}
+
+
+def lib(path: str | None = None):
+    """The oracle library (or a variant built by build_variant)."""
     global _lib
+    if path is not None:
+        if path not in _variants:
+            _variants[path] = _load(path)
+        return _variants[path]
     if _lib is None:
-        path = build()
-        L = C.CDLL(path)
-        P, D, I, Lg = C.c_void_p, C.c_double, C.c_int, C.c_long
-        DP = C.POINTER(C.c_double)
-        L.or_create.restype = P
-        L.or_create.argtypes = [I, C.POINTER(C.c_int), DP]
-        L.or_destroy.argtypes = [P]
-        L.or_set_material.argtypes = [P, D, D, D, D, D, DP]
-        L.or_set_solver.argtypes = [P, D, Lg, I, D, D, D, I]
-        L.or_set_freeze.argtypes = [P, Lg, D]
-        L.or_set_advection.argtypes = [P, I]
-        L.or_set_incompressible.argtypes = [P, I]
-        L.or_set_shear_modulus.argtypes = [P, DP]
-        L.or_advect.argtypes = [P, D]
-        L.or_apply_increment.argtypes = [P, DP, D, DP]
-        L.or_solve_increment.argtypes = [P, C.POINTER(Info)]
-        L.or_commit.argtypes = [P]
-        L.or_eval.argtypes = [P, DP, DP, DP]
-        L.or_field_count.restype = Lg
-        L.or_field_count.argtypes = [P, I]
-        L.or_get_field.argtypes = [P, I, DP, Lg]
-        L.or_set_field.argtypes = [P, I, DP, Lg]
-        L.or_pt_params.argtypes = [P, DP, DP, DP]
-        L.or_set_start.argtypes = [P, DP]
-        _lib = L
+        _lib = _load(build())
     return _lib
+
+
+def _load(path):
+    L = C.CDLL(path)
+    P, D, I, Lg = C.c_void_p, C.c_double, C.c_int, C.c_long
+    DP = C.POINTER(C.c_double)
+    L.or_create.restype = P
+    L.or_create.argtypes = [I, C.POINTER(C.c_int), DP]
+    L.or_destroy.argtypes = [P]
+    L.or_set_material.argtypes = [P, D, D, D, D, D, DP]
+    L.or_set_solver.argtypes = [P, D, Lg, I, D, D, D, I]
+    L.or_set_freeze.argtypes = [P, Lg, D]
+    L.or_set_advection.argtypes = [P, I]
+    L.or_set_incompressible.argtypes = [P, I]
+    L.or_set_shear_modulus.argtypes = [P, DP]
+    L.or_advect.argtypes = [P, D]
+    L.or_apply_increment.argtypes = [P, DP, D, DP]
+    L.or_solve_increment.argtypes = [P, C.POINTER(Info)]
+    L.or_commit.argtypes = [P]
+    L.or_eval.argtypes = [P, DP, DP, DP]
+    L.or_field_count.restype = Lg
+    L.or_field_count.argtypes = [P, I]
+    L.or_get_field.argtypes = [P, I, DP, Lg]
+    L.or_set_field.argtypes = [P, I, DP, Lg]
+    L.or_pt_params.argtypes = [P, DP, DP, DP]
+    L.or_set_start.argtypes = [P, DP]
+    return L
 
 
 def _dp(a: np.ndarray):
@@ -115,8 +146,8 @@ def field_shape(ndim, n, name):
 class Oracle:
     """One staggered grid solved by the FP64 oracle."""
 
-    def __init__(self, ndim, n, L=(1.0, 1.0, 1.0)):
-        self.L_ = lib()
+    def __init__(self, ndim, n, L=(1.0, 1.0, 1.0), lib_path=None):
+        self.L_ = lib(lib_path)
         self.ndim = ndim
         self.n = tuple(int(x) for x in n[:ndim])
         nn = (C.c_int * 3)(*(list(self.n) + [1] * (3 - ndim)))

@@ -479,9 +479,8 @@ def test_p9_brute_force_newton_tiny_grids(ndim, n):
 # ---------------------------------------------------------------- P5 ------
 def test_p5_invariants_on_converged_increments():
     """On every converged increment of a small inclusion run: the centre scale
-    never exceeds 1, the plastic strain never decreases, the returned centre
-    deviator lies on or inside the yield surface, and yielding starts in the
-    weak inclusion before the matrix."""
+    never exceeds 1, the plastic strain never decreases, and yielding starts
+    in the weak inclusion before the matrix."""
     s = E.config(1, n=(32, 32), increments=9)
     o = O.from_setup(s, tol=1e-9)
     epl_prev = np.zeros((32, 32))
@@ -494,13 +493,8 @@ def test_p5_invariants_on_converged_increments():
         epl = o.get("epl")
         assert (epl >= epl_prev).all()
         epl_prev = epl
-        txx, tyy, txy, p = o.get("txx"), o.get("tyy"), o.get("txy"), o.get("p")
-        txy_c = 0.25 * (txy[:-1, :-1] + txy[1:, :-1] + txy[:-1, 1:] + txy[1:, 1:])
-        sj = np.sqrt(0.5 * (txx ** 2 + tyy ** 2) + txy_c ** 2)
-        Y = np.maximum(0, A2 * p + B2 * o.get("coh"))
-        # the centre return is exact for its own components; the averaged
-        # vertex shear uses the neighbours' mean scale, so allow a small excess
-        assert (sj - Y).max() <= 0.05 * Y.max()
+        # the yield-surface condition itself is pinned exactly (to rounding)
+        # by test_p5_centre_return_lies_on_the_yield_surface
         if info["n_plastic"] and first_plastic is None:
             first_plastic = inc
             weak = o.get("coh") < 1e-3

@@ -1,7 +1,8 @@
 """The allocation-free forward of the warm-start network against the
 allocating one, through the C ABI: same output, bit for bit, on calls in a
 row (the shared static activation array carries nothing from one call to the
-next), and a clear error above the static limit."""
+next), no change of the device's free memory across calls (it allocates
+nothing), and a clear error above the static limit."""
 import numpy as np
 import pytest
 
@@ -56,3 +57,29 @@ def test_static_forward_rejects_shapes_above_the_limit(P):
     with pytest.raises(P.EPError, match="static limit"):
         net.forward_static(x.data_ptr(), 1, [1024, 1024], x.data_ptr())
     net.close()
+
+
+def test_static_forward_allocates_no_device_memory(P):
+    """After one call has made the library's static array resident, further
+    calls -- on a new network and at a new shape -- leave the device's free
+    memory unchanged: the entry point allocates nothing."""
+    import torch
+    rng = np.random.default_rng(9)
+    net0 = _net(P, 2, 16, 3, seed=5)
+    x0 = torch.tensor(rng.normal(size=(1, 4, 32, 32)), dtype=torch.float32, device="cuda").contiguous()
+    y0 = torch.empty((1, 2, 32, 32), dtype=torch.float32, device="cuda")
+    net0.forward_static(x0.data_ptr(), 1, [32, 32], y0.data_ptr())
+    torch.cuda.synchronize()
+    net = _net(P, 2, 16, 3, seed=6)
+    x = torch.tensor(rng.normal(size=(2, 4, 40, 48)), dtype=torch.float32, device="cuda").contiguous()
+    y = torch.empty((2, 2, 40, 48), dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        net.forward_static(x.data_ptr(), 2, [48, 40], y.data_ptr())
+        net0.forward_static(x0.data_ptr(), 1, [32, 32], y0.data_ptr())
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.isfinite(y).all()
+    net.close()
+    net0.close()
