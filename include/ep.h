@@ -245,7 +245,12 @@ ep_status ep_net_forward(ep_net_handle n, const float *x, int N, const int size[
  * GPU (different streams with no ordering between them) race on it.  Nothing
  * in it has to start at zero.  The first call on a device looks up the
  * array's address with that device current; make it before any stream
- * capture.  Arguments, layout and stream are those of ep_net_forward. */
+ * capture.  The array is part of the library image: every device context in
+ * which the library is loaded holds its 64 MiB, whether or not this entry
+ * point is called.  The looked-up address is kept for the life of the
+ * process, so resetting the device (cudaDeviceReset) and then calling this
+ * again is not supported.  Arguments, layout and stream are those of
+ * ep_net_forward. */
 #define EP_NET_STATIC_FLOATS (16LL * 1024 * 1024)
 ep_status ep_net_forward_static(ep_net_handle n, const float *x, int N, const int size[3], float *y);
 /* MSE loss mean((net(x) - t)^2) and its parameter gradient (host, nullable) */

@@ -1160,6 +1160,7 @@ struct ep_batch {
   int4 *items = nullptr;
   DevInfo *dinfo = nullptr, *hinfo = nullptr;
   cudaGraphExec_t chunk = nullptr;
+  int chunk_nchk = 0;          // n_chk the captured chunk was built with
   double dt = 0.0;
   std::vector<double> a;
   std::string err;
@@ -1199,11 +1200,32 @@ ep_status batch_upload(ep_batch *b) {
   return EP_OK;
 }
 
+// A pair of CUDA events destroyed on every exit path.
+struct EventPair {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t create() {
+    cudaError_t e = cudaEventCreate(&e0);
+    return e == cudaSuccess ? cudaEventCreate(&e1) : e;
+  }
+  ~EventPair() {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  }
+};
+
+// The chunk graph holds n_chk sweeps; every member must use the same n_chk
+// (ep_set_solver may have changed one since ep_create_batch), and a chunk
+// captured with another n_chk is rebuilt.  The iteration cap (max_iter) is
+// taken from the first grid.
 template <typename T>
 ep_status batch_capture(ep_batch *b) {
-  if (b->chunk) return EP_OK;
-  cudaGraph_t graph;
   const int nchk = b->g[0]->opts.n_chk;
+  for (int q = 1; q < b->count; ++q)
+    if (b->g[q]->opts.n_chk != nchk)
+      return bfail(b, EP_ERR_STATE, "batch solve: the grids' n_chk differ (ep_set_solver changed one after ep_create_batch)");
+  if (b->chunk && b->chunk_nchk == nchk) return EP_OK;
+  if (b->chunk) { cudaGraphExecDestroy(b->chunk); b->chunk = nullptr; }
+  cudaGraph_t graph;
   BCK(b, cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
   for (int it = 0; it < nchk; ++it) {
     launch_fused2d<T>(b->tile, (const Inst2<T> *)b->insts, b->items, b->n_items, it & 1, it == 0, b->blocks, b->cap);
@@ -1214,6 +1236,7 @@ ep_status batch_capture(ep_batch *b) {
   e = cudaGraphInstantiate(&b->chunk, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return bfail(b, EP_ERR_CUDA, std::string("batch instantiate: ") + cudaGetErrorString(e));
+  b->chunk_nchk = nchk;
   return EP_OK;
 }
 
@@ -1221,9 +1244,9 @@ template <typename T>
 ep_status batch_solve(ep_batch *b, ep_solve_info *infos) {
   ep_status r = batch_capture<T>(b);
   if (r != EP_OK) return r;
-  cudaEvent_t e0, e1;
-  BCK(b, cudaEventCreate(&e0));
-  BCK(b, cudaEventCreate(&e1));
+  EventPair ev;
+  BCK(b, ev.create());
+  cudaEvent_t e0 = ev.e0, e1 = ev.e1;
   launch_init_batch<T>((const Inst2<T> *)b->insts, b->count, b->g[0]->opts.max_iter, b->stream);
   BCK(b, cudaEventRecord(e0, b->stream));
   const long long max_chunks = b->g[0]->opts.max_iter / b->g[0]->opts.n_chk + 2;
@@ -1239,8 +1262,6 @@ ep_status batch_solve(ep_batch *b, ep_solve_info *infos) {
   BCK(b, cudaEventSynchronize(e1));
   float ms = 0.f;
   cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   ep_status worst = EP_OK;
   for (int q = 0; q < b->count; ++q) {
     ep_grid *h = b->g[q];
@@ -1340,9 +1361,9 @@ ep_status ep_batch_autotune(ep_batch_handle b, int iters, int *tile_out) {
   if (!b || iters < 1) return bfail(b, EP_ERR_ARG, "ep_batch_autotune: bad arguments");
   for (int q = 0; q < b->count; ++q)
     if (!b->g[q]->in_increment) return bfail(b, EP_ERR_STATE, "ep_batch_autotune: apply an increment first");
-  cudaEvent_t e0, e1;
-  BCK(b, cudaEventCreate(&e0));
-  BCK(b, cudaEventCreate(&e1));
+  EventPair ev;
+  BCK(b, ev.create());
+  cudaEvent_t e0 = ev.e0, e1 = ev.e1;
   float best = 1e30f;
   int best_tile = 0;
   for (int tile = 0; tile < FUSED2D_TILES; ++tile) {
@@ -1367,8 +1388,6 @@ ep_status ep_batch_autotune(ep_batch_handle b, int iters, int *tile_out) {
     cudaEventElapsedTime(&ms, e0, e1);
     if (ms < best) { best = ms; best_tile = tile; }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   b->tile = best_tile;
   ep_status r = b->prec == EP_FP64 ? batch_upload<double>(b) : batch_upload<float>(b);
   if (r != EP_OK) return r;
@@ -1386,9 +1405,9 @@ ep_status ep_batch_time_sweep(ep_batch_handle b, int iters, double *ms_per_sweep
   // clear the records of the last solve (a converged grid would be skipped)
   if (b->prec == EP_FP64) launch_init_batch<double>((const Inst2<double> *)b->insts, b->count, 0, b->stream);
   else launch_init_batch<float>((const Inst2<float> *)b->insts, b->count, 0, b->stream);
-  cudaEvent_t e0, e1;
-  BCK(b, cudaEventCreate(&e0));
-  BCK(b, cudaEventCreate(&e1));
+  EventPair ev;
+  BCK(b, ev.create());
+  cudaEvent_t e0 = ev.e0, e1 = ev.e1;
   for (int it = 0; it <= iters; ++it) {   // one untimed sweep, then `iters` timed ones
     if (it == 1) BCK(b, cudaEventRecord(e0, b->stream));
     if (b->prec == EP_FP64)
@@ -1403,8 +1422,6 @@ ep_status ep_batch_time_sweep(ep_batch_handle b, int iters, double *ms_per_sweep
   BCK(b, cudaGetLastError());
   float ms = 0.f;
   cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   *ms_per_sweep = (double)ms / iters;
   // the timed sweeps advanced the iterates: start the increments again
   return b->prec == EP_FP64 ? batch_restart<double>(b) : batch_restart<float>(b);

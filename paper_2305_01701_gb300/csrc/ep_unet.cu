@@ -228,17 +228,40 @@ __global__ void k_slot_copy(const float *src, float *dst, int N, int C, int csrc
   if (accumulate) *d += val; else *d = val;
 }
 
-// MSE loss between y and target (both N x C x nv): grad = 2 (y - t) / count
-__global__ void k_mse(const float *y, const float *t, float *g, long long n, double *loss) {
-  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+// MSE loss between y and target (both N x C x nv): grad = 2 (y - t) / count.
+// The loss is summed in a fixed order so that it is the same bit for bit on
+// every call: a fixed grid of MSE_BLOCKS blocks strides over the elements,
+// each block reduces its threads' sums in a fixed tree into partial[block],
+// and k_mse_final adds the partials in a fixed tree.
+constexpr int MSE_BLOCKS = 256;
+
+__device__ __forceinline__ double block_sum_fixed(double v, double *sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) s += sh[w2];
+  return s;
+}
+
+__global__ void k_mse(const float *y, const float *t, float *g, long long n, double *partial) {
+  __shared__ double sh[NT / 32];
   double d2 = 0.0;
-  if (i < n) {
-    float d = y[i] - t[i];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float d = y[i] - t[i];
     g[i] = 2.f * d / (float)n;
-    d2 = (double)d * d;
+    d2 += (double)d * d;
   }
-  for (int o = 16; o > 0; o >>= 1) d2 += __shfl_xor_sync(0xffffffffu, d2, o);
-  if ((threadIdx.x & 31) == 0 && d2 != 0.0) atomicAdd(loss, d2 / (double)n);
+  const double s = block_sum_fixed(d2, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void k_mse_final(const double *partial, long long n, double *loss) {
+  __shared__ double sh[NT / 32];
+  const double s = block_sum_fixed(threadIdx.x < MSE_BLOCKS ? partial[threadIdx.x] : 0.0, sh);
+  if (threadIdx.x == 0) *loss = s / (double)n;
 }
 
 __global__ void k_adam(float *w, __nv_bfloat16 *wb, const float *g, float *m, float *v, long long n, float lr,
@@ -697,7 +720,7 @@ ep_status ep_net_create(int ndim, int in_ch, int out_ch, int base, int levels, u
   const long long np = u.nparam;
   if (cudaMalloc((void **)&u.w, np * 4) != cudaSuccess || cudaMalloc((void **)&u.g, np * 4) != cudaSuccess ||
       cudaMalloc((void **)&u.m, np * 4) != cudaSuccess || cudaMalloc((void **)&u.v, np * 4) != cudaSuccess ||
-      cudaMalloc((void **)&u.wb, np * 2) != cudaSuccess || cudaMalloc((void **)&u.dloss, 8) != cudaSuccess) {
+      cudaMalloc((void **)&u.wb, np * 2) != cudaSuccess || cudaMalloc((void **)&u.dloss, 8 * (1 + MSE_BLOCKS)) != cudaSuccess) {
     ep_net_destroy(n);
     return nfail(nullptr, EP_ERR_OOM, "ep_net_create: allocation failed");
   }
@@ -773,9 +796,9 @@ static ep_status net_grads(ep_net *n, const float *x, const float *t, int N, con
   if (u.D == 2) forward<2>(u, x); else forward<3>(u, x);
   const Idx I = indices(u);
   const long long no = (long long)N * u.cout * vox(u, 0);
-  NCK(n, cudaMemsetAsync(u.dloss, 0, 8, u.st));
   NCK(n, cudaMemsetAsync(u.g, 0, u.nparam * 4, u.st));
-  k_mse<<<nblk(no), NT, 0, u.st>>>(u.act[I.out], t, u.grad[I.out], no, u.dloss);
+  k_mse<<<MSE_BLOCKS, NT, 0, u.st>>>(u.act[I.out], t, u.grad[I.out], no, u.dloss + 1);
+  k_mse_final<<<1, NT, 0, u.st>>>(u.dloss + 1, no, u.dloss);
   if (u.D == 2) backward<2>(u, x); else backward<3>(u, x);
   NCK(n, cudaGetLastError());
   if (loss) NCK(n, cudaMemcpyAsync(loss, u.dloss, 8, cudaMemcpyDeviceToHost, u.st));

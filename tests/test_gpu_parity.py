@@ -209,6 +209,7 @@ def run_fp32_vs_oracle(P, s, increments, gpu_tol=1e-6, oracle_tol=1e-10, kernel=
         sc = group_scales(o, fields)
         for f in fields:
             worst[f] = max(worst.get(f, 0.0), rel_err(g.get(f), o.get(f), sc[f]))
+    worst["epl_max"] = float(np.abs(o.get("epl")).max())
     g.close()
     return worst
 
@@ -241,6 +242,37 @@ def test_fp32_mixed_within_stated_bounds_3d(P):
     for f in ("txx", "tyy", "tzz", "txy", "txz", "tyz", "p"):
         assert worst[f] <= 1e-5, (f, worst[f])
     assert worst["epl"] <= 1e-4, worst["epl"]
+
+
+def test_fp32_register_kernel_interior_windows_against_oracle(P):
+    """The benchmarked FP32 3D sweep (register z-march) on a grid with several
+    interior windows, whose copy of the body skips the domain-boundary tests
+    and takes untested clamped loads, against the FP64 oracle through first
+    yield of the inclusion (which lies inside those windows): stress within
+    1e-5 and plastic strain within 1e-4.  A window is 32 x 16 columns with
+    28 x 12 written; on 90 x 40 columns the windows at x-blocks 1-2 and
+    y-blocks 1-2 are interior."""
+    nx, ny, nz = 90, 40, 24
+    s = E.config(3, n=(nx, ny, nz), L=(1.0, ny / nx, nz / nx), inclusion_radius=0.06)
+    worst = run_fp32_vs_oracle(P, s, 6, kernel=(P.KERNEL_FUSED_REG, 0))
+    for f in ("txx", "tyy", "tzz", "txy", "txz", "tyz", "p"):
+        assert worst[f] <= 1e-5, (f, worst[f])
+    assert worst["epl"] <= 1e-4, worst["epl"]
+    assert worst["epl_max"] > 0
+
+
+@pytest.mark.parametrize("tile", [3, 4])
+def test_fp32_warp_strips_many_strips_and_segments_against_oracle(P, tile):
+    """The FP32 warp-strip 2D sweep on a grid of 6 full strips (28 columns)
+    plus a ragged one and several 64- or 32-row segments, against the FP64
+    oracle through first yield: stress within 1e-5, plastic strain within
+    1e-4."""
+    s = E.config(1, n=(180, 150), L=(1.0, 150 / 180), inclusion_radius=0.05)
+    worst = run_fp32_vs_oracle(P, s, 6, kernel=(P.KERNEL_FUSED, tile))
+    for f in ("txx", "tyy", "txy", "p"):
+        assert worst[f] <= 1e-5, (f, worst[f])
+    assert worst["epl"] <= 1e-4, worst["epl"]
+    assert worst["epl_max"] > 0
 
 
 def test_advection_fp64_parity_2d(P):
