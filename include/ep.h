@@ -48,7 +48,8 @@ typedef enum {
   EP_ERR_STATE = 4,          /* call out of order (e.g. solve w/o increment)*/
   EP_ERR_NOT_CONVERGED = 5,  /* max_iter reached; state kept                */
   EP_ERR_DIVERGED = 6,       /* NaN/Inf in a residual norm                  */
-  EP_ERR_TIMEOUT = 7         /* a bounded device wait gave up               */
+  EP_ERR_TIMEOUT = 7,        /* a bounded device wait gave up               */
+  EP_PENDING = 8             /* ep_solve_chunks: not decided yet, continue  */
 } ep_status;
 
 /* EP_FP64: every sweep in FP64.  EP_FP32_MIXED: sweeps in FP32 on the
@@ -162,6 +163,17 @@ ep_status ep_apply_increment_rates(ep_handle h, const double rates[3], double dt
  * NULL.  Returns EP_ERR_NOT_CONVERGED / EP_ERR_DIVERGED without committing. */
 ep_status ep_solve_increment(ep_handle h, ep_solve_info *info);
 
+/* Iterate the open increment for at most max_chunks chunks of n_chk
+ * iterations (Sec. 3.2, the pseudo-time loop of Fig. 1, cut into pieces).
+ * Returns EP_PENDING when the stopping test has not decided yet: the iterate,
+ * the convergence record and the frozen-plasticity state are kept and the
+ * next call continues the same iteration (info->iters is then the next check
+ * iteration, info->ms the device time of this call).  Otherwise it returns
+ * what ep_solve_increment returns and commits on convergence.  Calling it
+ * until the status is not EP_PENDING performs exactly the iterations of one
+ * ep_solve_increment; applying a new increment abandons an undecided solve. */
+ep_status ep_solve_chunks(ep_handle h, int max_chunks, ep_solve_info *info);
+
 /* Commit the current iterate as the increment's result (used after a
  * deliberate fixed-iteration solve). */
 ep_status ep_commit_increment(ep_handle h);
@@ -262,25 +274,52 @@ ep_status ep_net_train_step(ep_net_handle n, const float *x, const float *t, int
 ep_status ep_net_destroy(ep_net_handle n);
 const char *ep_net_last_error(ep_net_handle n);
 
-/* Attach a network (ndim spatial dims, ndim + 2 inputs, ndim outputs; NULL
- * detaches) used by ep_apply_increment(..., use_warm_start = 1).  Features
- * at cell centres, on a grid padded to multiples of 4: the previous
- * increment's velocity change (centre average per component) over its
- * L-infinity norm S, then 1 - s (the last return scale), then c / max(c).
- * The start velocity becomes v + S (dv_prev + net output interpolated to the
- * faces); with fewer than two committed increments the plain start is used.
- * The network does not change the converged answer, only the start. */
-ep_status ep_attach_warm_start(ep_handle h, ep_net_handle net);
-/* The features of the next increment (device, (ndim + 2) x padded size) and
- * their scale S; dims receives the padded size {X, Y, Z}. */
-ep_status ep_warm_features(ep_handle h, float *dev_out, double *scale, int dims[3]);
-/* After a solve: the training target for features f taken before it
- * (device, ndim x padded size): centre average of the committed velocity
- * change over S, minus the feature channels of the previous change. */
-ep_status ep_warm_target(ep_handle h, const float *features, double scale, float *dev_out);
+/* The learned warm start (the method's extension (a); the paper's own
+ * iteration, Sec. 3.2, starts every increment from the previous one).  The
+ * network works on a grid of coarse cells, each the mean of coarsen^D fine
+ * cells, padded with zeros to a multiple of 4 cells per side
+ * (ep_warm_dims).  Tensors are FP32, channels x [Z x] Y x X, x fastest.
+ * Input channels (EP_WARM_IN: 13 in 3D, 9 in 2D), at cell centres:
+ *   the previous increment's velocity change (centre mean per component)
+ *   over S_v; the old deviator, normal components and shear components
+ *   averaged from the 4 surrounding vertices/edges, over the cell's cohesion
+ *   c; the old pressure over c; 1 - s (the last return scale); c / max c;
+ *   the accumulated plastic strain over S_e.
+ * Output channels (EP_WARM_OUT: 9 in 3D, 5 in 2D): the increment's velocity
+ *   change over S_v (nd), then the converged pseudo-time stress state minus
+ *   the physical response of the converged velocity over S_t (normal
+ *   components, then shear components averaged to the centre).
+ * S_v = 0.1 |a| L_max, S_t = 2 G |a| dt, S_e = 10 |a| dt, |a| the largest
+ * loading rate of the grid's increment.  With a network attached,
+ * ep_apply_increment(..., use_warm_start = 1) starts the interior velocity at
+ * v + S_v * (velocity channels interpolated linearly from the coarse centres
+ * to the faces) and the pseudo-time stress state at the physical response of
+ * that velocity plus S_t * (stress channels interpolated to centres and
+ * interior vertices/edges).  A zero output reproduces the plain start; the
+ * iteration still runs to the same tolerance.  With fewer than two committed
+ * increments the plain start is used. */
+#define EP_WARM_IN(nd) ((nd) == 3 ? 13 : 9)
+#define EP_WARM_OUT(nd) ((nd) == 3 ? 9 : 5)
+/* Padded coarse size {X, Y, Z} (Z = 1 in 2D) for coarsening factor coarsen. */
+ep_status ep_warm_dims(ep_handle h, int coarsen, int dims[3]);
+/* Attach a network with EP_WARM_IN(ndim) inputs and EP_WARM_OUT(ndim)
+ * outputs, applied at coarsening factor coarsen (>= 1); NULL detaches.  The
+ * network must outlive the attachment. */
+ep_status ep_attach_warm_start(ep_handle h, ep_net_handle net, int coarsen);
+/* Recording on (non-zero): every later commit also keeps the physical
+ * response of the converged velocity (one FP32 box per stress component,
+ * allocated here), which ep_warm_target needs. */
+ep_status ep_warm_record(ep_handle h, int on);
+/* The features of the next increment at coarsening coarsen (device,
+ * EP_WARM_IN x padded size).  Needs two committed increments. */
+ep_status ep_warm_features(ep_handle h, int coarsen, float *dev_out);
+/* After a recorded solve: that increment's target (device, EP_WARM_OUT x
+ * padded size). */
+ep_status ep_warm_target(ep_handle h, int coarsen, float *dev_out);
 
-/* Device-resident checkpoint of the FP64 history (velocity, deviator,
- * pressure, plastic strain, displacement, accumulated strain).  The first
+/* Device-resident checkpoint of the FP64 history (velocity and the one
+ * before it, deviator, pressure, plastic strain, displacement, accumulated
+ * strain) and of the last return scale (a warm-start feature).  The first
  * ep_snapshot allocates the checkpoint with cudaMalloc (freed by ep_destroy);
  * ep_restore copies it back, so the next increment starts from the saved
  * state.  Both run on the grid's stream and return after it has drained. */

@@ -116,6 +116,7 @@ def _load(path):
     L.or_set_field.argtypes = [P, I, DP, Lg]
     L.or_pt_params.argtypes = [P, DP, DP, DP]
     L.or_set_start.argtypes = [P, DP]
+    L.or_get_eval.argtypes = [P, I, DP, Lg]
     return L
 
 
@@ -219,6 +220,15 @@ class Oracle:
         mr, ms = C.c_double(), C.c_double()
         self._chk(self.L_.or_eval(self.h, _dp(v), C.byref(mr), C.byref(ms)), "eval")
         return mr.value, ms.value
+
+    def eval_stress(self, name):
+        """A stress component of the last evaluation ("txx".."tyz", "p"), in
+        the field's shape: after eval(v), the physical response of v."""
+        comp = {"txx": 0, "tyy": 1, "tzz": 2, "txy": 3, "txz": 4, "tyz": 5, "p": 6}[name]
+        shape = field_shape(self.ndim, self.n + (1,), name)
+        out = np.empty(int(np.prod(shape)), dtype=np.float64)
+        self._chk(self.L_.or_get_eval(self.h, comp, _dp(out), out.size), "get_eval " + name)
+        return out.reshape(shape)
 
     def commit(self):
         self._chk(self.L_.or_commit(self.h), "commit")

@@ -981,6 +981,27 @@ int or_eval(or_grid *g, const double *v, double *max_r, double *max_sig) {
   return OR_OK;
 }
 
+/* The stress of the last evaluation (or_eval gives the physical response of
+ * a velocity): comp 0..2 the centre deviator components, 3..5 the shear
+ * components (vertices/edges), 6 the pressure. */
+int or_get_eval(or_grid *g, int comp, double *out, long count) {
+  if (!g->evaluated || comp < 0 || comp > 6) return OR_ERR_STATE;
+  const double *src;
+  long n;
+  if (comp < 3) {
+    if (comp >= g->ndim) return OR_ERR_ARG;
+    src = g->sn[comp]; n = n_centres(g);
+  } else if (comp < 6) {
+    if (comp - 3 >= n_shear_comp(g)) return OR_ERR_ARG;
+    src = g->ss[comp - 3]; n = n_shear(g, comp - 3);
+  } else {
+    src = g->pc; n = n_centres(g);
+  }
+  if (count != n) return OR_ERR_ARG;
+  memcpy(out, src, sizeof(double) * n);
+  return OR_OK;
+}
+
 /* A9 history commit from the last evaluation at the converged iterate:
  * tau_hat <- tau, p_hat <- p; at centres where the return acted (s < 1) the
  * plastic strain grows by dt times the magnitude sqrt(J2) of the plastic

@@ -17,7 +17,18 @@ LIB_PATH = os.path.join(_HERE, "lib", "libep.so")
 
 OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_STATE, ERR_NOT_CONVERGED, ERR_DIVERGED, ERR_TIMEOUT = range(8)
 STATUS_NAMES = {0: "EP_OK", 1: "EP_ERR_ARG", 2: "EP_ERR_CUDA", 3: "EP_ERR_OOM", 4: "EP_ERR_STATE",
-                5: "EP_ERR_NOT_CONVERGED", 6: "EP_ERR_DIVERGED", 7: "EP_ERR_TIMEOUT"}
+                5: "EP_ERR_NOT_CONVERGED", 6: "EP_ERR_DIVERGED", 7: "EP_ERR_TIMEOUT", 8: "EP_PENDING"}
+PENDING = 8
+
+
+def warm_in(ndim):
+    """Input channels of the warm-start network (EP_WARM_IN)."""
+    return 13 if ndim == 3 else 9
+
+
+def warm_out(ndim):
+    """Output channels of the warm-start network (EP_WARM_OUT)."""
+    return 9 if ndim == 3 else 5
 FP64, FP32_MIXED = 0, 1
 LOAD_XY, LOAD_XZ = 0, 1
 KERNEL_AUTO, KERNEL_STAGED, KERNEL_FUSED, KERNEL_FUSED_TMA, KERNEL_FUSED_REG = -1, 0, 1, 2, 3
@@ -66,6 +77,7 @@ SIGNATURES = [
     ("ep_apply_increment", _I, [_P, _D, _D, _I, _DP, _I]),
     ("ep_apply_increment_rates", _I, [_P, _DP, _D, _DP, _DP]),
     ("ep_solve_increment", _I, [_P, C.POINTER(SolveInfo)]),
+    ("ep_solve_chunks", _I, [_P, _I, C.POINTER(SolveInfo)]),
     ("ep_commit_increment", _I, [_P]),
     ("ep_field_count", _I, [_P, _I, C.POINTER(C.c_size_t)]),
     ("ep_get_fields", _I, [_P, _I, _DP, _Z]),
@@ -88,9 +100,11 @@ SIGNATURES = [
     ("ep_net_train_step", _I, [_P, _P, _P, _I, _IP, C.c_float, C.POINTER(C.c_double)]),
     ("ep_net_destroy", _I, [_P]),
     ("ep_net_last_error", C.c_char_p, [_P]),
-    ("ep_attach_warm_start", _I, [_P, _P]),
-    ("ep_warm_features", _I, [_P, _P, C.POINTER(C.c_double), _IP]),
-    ("ep_warm_target", _I, [_P, _P, _D, _P]),
+    ("ep_attach_warm_start", _I, [_P, _P, _I]),
+    ("ep_warm_dims", _I, [_P, _I, _IP]),
+    ("ep_warm_record", _I, [_P, _I]),
+    ("ep_warm_features", _I, [_P, _I, _P]),
+    ("ep_warm_target", _I, [_P, _I, _P]),
     ("ep_snapshot", _I, [_P]),
     ("ep_restore", _I, [_P]),
     ("ep_time_sweep", _I, [_P, _I, _DP, _I, _IP]),
@@ -233,6 +247,17 @@ class Grid:
         d["status"] = st
         return d
 
+    def solve_chunks(self, max_chunks=1, raise_on_fail=True):
+        """At most max_chunks chunks of the open increment's iteration; the
+        returned dict's "status" is PENDING while the solve is undecided."""
+        info = SolveInfo()
+        st = self._L.ep_solve_chunks(self.h, int(max_chunks), C.byref(info))
+        if raise_on_fail and st != PENDING:
+            check(self.h, st)
+        d = info.as_dict()
+        d["status"] = st
+        return d
+
     def commit_increment(self):
         check(self.h, self._L.ep_commit_increment(self.h))
 
@@ -255,25 +280,35 @@ class Grid:
     def snapshot(self):
         check(self.h, self._L.ep_snapshot(self.h))
 
-    def attach_warm_start(self, net):
-        check(self.h, self._L.ep_attach_warm_start(self.h, net.h if net is not None else None))
+    def attach_warm_start(self, net, coarsen=1):
+        """Use `net` (EP_WARM_IN inputs, EP_WARM_OUT outputs) at coarsening
+        `coarsen` for ep_apply_increment(..., use_warm_start=True)."""
+        check(self.h, self._L.ep_attach_warm_start(self.h, net.h if net is not None else None, int(coarsen)))
 
-    def warm_dims(self):
-        p = [(x + 3) // 4 * 4 for x in self.n]
-        return tuple(p + [1] * (3 - len(p)))
-
-    def warm_features(self, out_ptr):
-        """Write the next increment's features to device memory at out_ptr; returns S."""
-        sc = C.c_double()
+    def warm_dims(self, coarsen=1):
+        """Padded coarse grid {X, Y, Z} of the warm-start tensors."""
         dims = (C.c_int * 3)()
-        check(self.h, self._L.ep_warm_features(self.h, out_ptr, C.byref(sc), dims))
-        return sc.value
+        check(self.h, self._L.ep_warm_dims(self.h, int(coarsen), dims))
+        return tuple(dims)
 
-    def warm_target(self, feat_ptr, scale, out_ptr):
-        check(self.h, self._L.ep_warm_target(self.h, feat_ptr, scale, out_ptr))
+    def warm_record(self, on=True):
+        """Keep what ep_warm_target needs at every later commit."""
+        check(self.h, self._L.ep_warm_record(self.h, int(bool(on))))
+
+    def warm_features(self, out_ptr, coarsen=1):
+        """Write the next increment's features to device memory at out_ptr."""
+        check(self.h, self._L.ep_warm_features(self.h, int(coarsen), out_ptr))
+
+    def warm_target(self, out_ptr, coarsen=1):
+        """Write the last recorded increment's target to device memory at out_ptr."""
+        check(self.h, self._L.ep_warm_target(self.h, int(coarsen), out_ptr))
 
     def restore(self):
         check(self.h, self._L.ep_restore(self.h))
+
+    def set_from(self, name, host_ptr, count):
+        """Copy a history field from caller memory at host_ptr (e.g. pinned torch storage)."""
+        check(self.h, self._L.ep_set_fields(self.h, FIELD_ID[name], C.cast(host_ptr, _DP), count))
 
     def get_into(self, name, host_ptr, count):
         """Copy a field into caller memory at host_ptr (e.g. pinned torch storage)."""

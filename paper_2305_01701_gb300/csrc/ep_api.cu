@@ -38,6 +38,7 @@ struct ep_grid {
   ep_solver_opts opts{};
   double rate[3] = {0, 0, 0}, dt = 0;
   bool in_increment = false, started = false, have_f = false;
+  bool solving = false;          // a solve of the open increment is under way (ep_solve_chunks)
   History H{};
   // FP64 scratch
   double *om64[3] = {}, *es64[3] = {}, *Tn64[3] = {}, *Ts64[3] = {}, *s64 = nullptr;
@@ -69,7 +70,10 @@ struct ep_grid {
   double cmax = 1.0;
   ep_net *net = nullptr;
   float *wx = nullptr, *wy = nullptr;   // network input / output (cudaMalloc on attach)
-  unsigned long long *wscale = nullptr;
+  int wcoarse = 1;              // coarsening factor of the attached network's grid
+  bool warm_stress = false;     // the next prologue adds the predicted stress state
+  bool wrecord = false;         // commits record the physical response (training targets)
+  float *w0 = nullptr;          // that response, (nd + ns) FP32 boxes (cudaMalloc)
   char *snap = nullptr;     // checkpoint of the history (ep_snapshot)
   bool snap_started = false;
   int snap_commits = 0, snap_adv_done = 0;
@@ -172,7 +176,6 @@ void carve(ep_grid *h, Arena &a) {
   h->items_dev = a.take<int4>(h->max_items);
   h->dnpl = a.take<unsigned long long>(1);
   h->dline = a.take<double>(2);
-  h->wscale = a.take<unsigned long long>(1);
 }
 
 // natural extent of a field id; returns false for an unknown / absent field
@@ -374,6 +377,26 @@ Stage<double> phys_stage(ep_grid *h, double *const v[3]) {
   return S;
 }
 
+// padded size of the warm-start network's grid at coarsening f
+void warm_dims(const ep_grid *h, int f, int dims[3]) {
+  dims[0] = ((h->g.nx + f - 1) / f + 3) / 4 * 4;
+  dims[1] = ((h->g.ny + f - 1) / f + 3) / 4 * 4;
+  dims[2] = h->ndim == 3 ? ((h->g.nz + f - 1) / f + 3) / 4 * 4 : 1;
+}
+
+WarmScales warm_scales(const ep_grid *h) {
+  double a = 0.0, Lm = 0.0;
+  for (int d = 0; d < h->ndim; ++d) { a = std::max(a, fabs(h->rate[d])); Lm = std::max(Lm, h->L[d]); }
+  if (!(a > 0.0)) a = 1.0;
+  const double dt = h->dt > 0.0 ? h->dt : 1.0;
+  WarmScales w;
+  w.sv_inv = 1.0 / (0.1 * a * Lm);
+  w.st_inv = 1.0 / (2.0 * h->G * a * dt);
+  w.se_inv = 1.0 / (10.0 * a * dt);
+  w.cmax_inv = 1.0 / h->cmax;
+  return w;
+}
+
 template <typename Td>
 ep_status copy_into(ep_grid *h, void *dst, const double *src) {
   if (sizeof(Td) == 8) {
@@ -410,6 +433,12 @@ ep_status prologue(ep_grid *h, const double *const dv[3]) {
   launch_trial<double>(g, S, h->dscal, nullptr, st);
   launch_return_centres<double>(g, S, h->dscal, nullptr, 0, st);
   launch_return_edges<double>(g, S, h->dscal, nullptr, 0, st);
+  if (h->warm_stress && h->net) {
+    // learned warm start: the predicted relaxed-return part of the state
+    int dims[3];
+    warm_dims(h, h->wcoarse, dims);
+    launch_warm_stress(g, h->wy, h->wcoarse, 1.0 / warm_scales(h).st_inv, h->stn64, h->sts64, dims, st);
+  }
   CK(h, cudaGetLastError());
   // sweep constants: base trial tau_tr(v0), base pressure p(v0), weights
   const int nd = h->ndim, ns = n_shear(nd);
@@ -530,6 +559,13 @@ ep_status commit(ep_grid *h) {
   Stage<double> S = phys_stage(h, h->H.v);
   launch_strain<double>(g, S, h->dscal, nullptr, st);
   launch_trial<double>(g, S, h->dscal, nullptr, st);
+  if (h->wrecord && h->w0) {
+    // the physical response of the converged velocity with the old history
+    // (warm-start training targets); the trial stays in Tn64 / Ts64
+    launch_return_centres<double>(g, S, h->dscal, nullptr, 0, st);
+    launch_return_edges<double>(g, S, h->dscal, nullptr, 0, st);
+    launch_warm_record(g, h->stn64, h->sts64, h->w0, st);
+  }
   CK(h, cudaMemsetAsync(h->dnpl, 0, sizeof(unsigned long long), st));
   const T *stn[3] = {P<T>(h->stn[1][0]), P<T>(h->stn[1][1]), P<T>(h->stn[1][2])};
   const T *sts[3] = {P<T>(h->sts[1][0]), P<T>(h->sts[1][1]), P<T>(h->sts[1][2])};
@@ -538,28 +574,53 @@ ep_status commit(ep_grid *h) {
   launch_line_integrals(g, h->H, h->dline, st);
   CK(h, cudaGetLastError());
   h->in_increment = false;
+  h->solving = false;
   h->n_commits += 1;
   return EP_OK;
 }
 
+// Iterate the open increment for at most max_chunks chunks.  The first call
+// of an increment starts the convergence record; a call that ends before the
+// record is decided returns EP_PENDING and the next call continues the same
+// iteration (the state sits in buffer 0 after every whole chunk, n_chk being
+// even).  The decided call commits on convergence.
 template <typename T>
-ep_status solve(ep_grid *h, ep_solve_info *info) {
+ep_status solve(ep_grid *h, long long max_chunks, ep_solve_info *info) {
   ep_status r = capture_chunk<T>(h);
   if (r != EP_OK) return r;
-  DevInfo init{};
-  init.max_iter = h->opts.max_iter;
-  init.frozen_at = -1;
-  *h->hinfo = init;
-  CK(h, cudaMemcpyAsync(h->dinfo, h->hinfo, sizeof(DevInfo), cudaMemcpyHostToDevice, h->stream));
+  if (!h->solving) {
+    DevInfo init{};
+    init.max_iter = h->opts.max_iter;
+    init.frozen_at = -1;
+    *h->hinfo = init;
+    CK(h, cudaMemcpyAsync(h->dinfo, h->hinfo, sizeof(DevInfo), cudaMemcpyHostToDevice, h->stream));
+    h->solving = true;
+  }
   CK(h, cudaEventRecord(h->ev0, h->stream));
-  const long long max_chunks = h->opts.max_iter / h->opts.n_chk + 2;
-  for (long long c = 0; c < max_chunks; ++c) {
+  const long long cap = h->opts.max_iter / h->opts.n_chk + 2;
+  bool decided = false;
+  for (long long c = 0; c < std::min(max_chunks, cap); ++c) {
     CK(h, cudaGraphLaunch(h->chunk, h->stream));
     CK(h, cudaMemcpyAsync(h->hinfo, h->dinfo, sizeof(DevInfo), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
-    if (h->hinfo->done) break;
+    if (h->hinfo->done) { decided = true; break; }
   }
   const DevInfo di = *h->hinfo;
+  if (!decided) {
+    CK(h, cudaEventRecord(h->ev1, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    float ms = 0.f;
+    CK(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+    if (info) {
+      memset(info, 0, sizeof(*info));
+      info->iters = di.k_check; info->eps_res = di.eps_res; info->eps_mom = di.eps_mom;
+      info->eps_tau = di.eps_tau; info->eps_p = di.eps_p; info->eps_rel = di.eps_rel;
+      info->max_r = di.max_r; info->max_sigma = di.max_sig; info->ms = ms; info->status = EP_PENDING;
+      info->frozen_at = di.frozen_at;
+    }
+    return EP_PENDING;
+  }
+  h->solving = false;
   ep_status st = di.done == 1 ? EP_OK : di.done == 2 ? EP_ERR_DIVERGED : di.done == 4 ? EP_ERR_TIMEOUT
                                                                                     : EP_ERR_NOT_CONVERGED;
   unsigned long long npl = 0;
@@ -772,6 +833,7 @@ static ep_status run_prologue(ep_grid *h, const double *const dv[3]) {
   CK(h, cudaStreamSynchronize(h->stream));
   h->started = true;
   h->in_increment = true;
+  h->solving = false;
   return EP_OK;
 }
 
@@ -805,71 +867,92 @@ static ep_status apply_common(ep_handle h, const double rates[3], double dt, con
   return run_prologue(h, dvh);
 }
 
-static void warm_dims(const ep_grid *h, int dims[3]) {
-  dims[0] = (h->g.nx + 3) / 4 * 4;
-  dims[1] = (h->g.ny + 3) / 4 * 4;
-  dims[2] = h->ndim == 3 ? (h->g.nz + 3) / 4 * 4 : 1;
-}
-
-static ep_status warm_features_into(ep_grid *h, float *x) {
+static ep_status warm_features_into(ep_grid *h, int f, float *x) {
   int dims[3];
-  warm_dims(h, dims);
-  launch_warm_scale(h->g, h->H, h->vpp, h->wscale, h->stream);
-  if (h->prec == EP_FP64) launch_warm_features<double>(h->g, h->H, h->vpp, P<double>(h->s), h->cmax, h->wscale, x, dims, h->stream);
-  else launch_warm_features<float>(h->g, h->H, h->vpp, P<float>(h->s), h->cmax, h->wscale, x, dims, h->stream);
+  warm_dims(h, f, dims);
+  const WarmScales ws = warm_scales(h);
+  if (h->prec == EP_FP64) launch_warm_features<double>(h->g, h->H, h->vpp, P<double>(h->s), ws, f, x, dims, h->stream);
+  else launch_warm_features<float>(h->g, h->H, h->vpp, P<float>(h->s), ws, f, x, dims, h->stream);
   CK(h, cudaGetLastError());
   return EP_OK;
 }
 
-// start velocity from the network's prediction (device end to end)
+// start from the network's prediction (device end to end): the velocity
+// channels give the start increment at the faces, the stress channels are
+// added to the physical response of that start velocity by the prologue
 static ep_status apply_warm(ep_grid *h, const double rates[3], double dt, const double *body_force) {
   int dims[3];
-  warm_dims(h, dims);
-  ep_status r = warm_features_into(h, h->wx);
+  const int f = h->wcoarse;
+  warm_dims(h, f, dims);
+  // the scales follow this increment's loading
+  for (int d = 0; d < 3; ++d) h->rate[d] = d < h->ndim ? rates[d] : 0.0;
+  h->dt = dt;
+  ep_status r = warm_features_into(h, f, h->wx);
   if (r != EP_OK) return r;
   CK(h, cudaStreamSynchronize(h->stream));
   r = ep_net_forward(h->net, h->wx, 1, dims, h->wy);
   if (r != EP_OK) return fail(h, r, std::string("warm start network: ") + ep_net_last_error(h->net));
   CK(h, cudaDeviceSynchronize());
+  const WarmScales ws = warm_scales(h);
   // Tn64 is free until the prologue's trial stage (after the start velocity)
   double *dv[3] = {h->Tn64[0], h->Tn64[1], h->ndim == 3 ? h->Tn64[2] : nullptr};
-  launch_warm_dv(h->g, h->H, h->vpp, h->wy, h->wscale, dv, dims, h->stream);
+  launch_warm_dv(h->g, h->wy, f, 1.0 / ws.sv_inv, dv, dims, h->stream);
   CK(h, cudaGetLastError());
-  return apply_common_dev(h, rates, dt, body_force, dv);
+  h->warm_stress = true;
+  r = apply_common_dev(h, rates, dt, body_force, dv);
+  h->warm_stress = false;
+  return r;
 }
 
-ep_status ep_attach_warm_start(ep_handle h, ep_net_handle net) {
+ep_status ep_warm_dims(ep_handle h, int coarsen, int dims[3]) {
+  if (!h || !dims || coarsen < 1) return fail(h, EP_ERR_ARG, "ep_warm_dims: bad arguments");
+  warm_dims(h, coarsen, dims);
+  return EP_OK;
+}
+
+ep_status ep_attach_warm_start(ep_handle h, ep_net_handle net, int coarsen) {
   if (!h) return fail(nullptr, EP_ERR_ARG, "null handle");
+  if (coarsen < 1) return fail(h, EP_ERR_ARG, "ep_attach_warm_start: coarsen must be >= 1");
   if (h->wx) { cudaFree(h->wx); h->wx = nullptr; }
   if (h->wy) { cudaFree(h->wy); h->wy = nullptr; }
   h->net = net;
+  h->wcoarse = coarsen;
   if (!net) return EP_OK;
   int dims[3];
-  warm_dims(h, dims);
+  warm_dims(h, coarsen, dims);
   const long long nv = (long long)dims[0] * dims[1] * dims[2];
-  CK(h, cudaMalloc((void **)&h->wx, nv * (h->ndim + 2) * sizeof(float)));
-  CK(h, cudaMalloc((void **)&h->wy, nv * h->ndim * sizeof(float)));
+  CK(h, cudaMalloc((void **)&h->wx, nv * warm_in_channels(h->ndim) * sizeof(float)));
+  CK(h, cudaMalloc((void **)&h->wy, nv * warm_out_channels(h->ndim) * sizeof(float)));
   return EP_OK;
 }
 
-ep_status ep_warm_features(ep_handle h, float *dev_out, double *scale, int dims[3]) {
-  if (!h || !dev_out) return fail(h, EP_ERR_ARG, "ep_warm_features: null argument");
+ep_status ep_warm_record(ep_handle h, int on) {
+  if (!h) return fail(nullptr, EP_ERR_ARG, "null handle");
+  if (on && !h->w0) {
+    const size_t n = (size_t)(h->ndim + n_shear(h->ndim)) * h->g.box;
+    CK(h, cudaMalloc((void **)&h->w0, n * sizeof(float)));
+    CK(h, cudaMemset(h->w0, 0, n * sizeof(float)));
+  }
+  if (!on && h->w0) { cudaFree(h->w0); h->w0 = nullptr; }
+  h->wrecord = on != 0;
+  return EP_OK;
+}
+
+ep_status ep_warm_features(ep_handle h, int coarsen, float *dev_out) {
+  if (!h || !dev_out || coarsen < 1) return fail(h, EP_ERR_ARG, "ep_warm_features: bad arguments");
   if (h->n_commits < 2) return fail(h, EP_ERR_STATE, "ep_warm_features: needs two committed increments");
-  ep_status r = warm_features_into(h, dev_out);
+  ep_status r = warm_features_into(h, coarsen, dev_out);
   if (r != EP_OK) return r;
-  unsigned long long b = 0;
-  CK(h, cudaMemcpyAsync(&b, h->wscale, sizeof(b), cudaMemcpyDeviceToHost, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
-  if (scale) memcpy(scale, &b, sizeof(double));
-  if (dims) warm_dims(h, dims);
   return EP_OK;
 }
 
-ep_status ep_warm_target(ep_handle h, const float *features, double scale, float *dev_out) {
-  if (!h || !features || !dev_out) return fail(h, EP_ERR_ARG, "ep_warm_target: null argument");
+ep_status ep_warm_target(ep_handle h, int coarsen, float *dev_out) {
+  if (!h || !dev_out || coarsen < 1) return fail(h, EP_ERR_ARG, "ep_warm_target: bad arguments");
+  if (!h->wrecord || h->n_commits < 1) return fail(h, EP_ERR_STATE, "ep_warm_target: record a committed increment first");
   int dims[3];
-  warm_dims(h, dims);
-  launch_warm_target(h->g, h->H, h->vpp, features, scale, dev_out, dims, h->stream);
+  warm_dims(h, coarsen, dims);
+  launch_warm_target(h->g, h->H, h->vpp, h->w0, warm_scales(h), coarsen, dev_out, dims, h->stream);
   CK(h, cudaGetLastError());
   CK(h, cudaStreamSynchronize(h->stream));
   return EP_OK;
@@ -896,7 +979,14 @@ ep_status ep_apply_increment(ep_handle h, double a, double dt, int load_plane, c
 ep_status ep_solve_increment(ep_handle h, ep_solve_info *info) {
   if (!h) return fail(nullptr, EP_ERR_ARG, "null handle");
   if (!h->in_increment) return fail(h, EP_ERR_STATE, "ep_solve_increment: apply an increment first");
-  return h->prec == EP_FP64 ? solve<double>(h, info) : solve<float>(h, info);
+  const long long all = 1ll << 62;
+  return h->prec == EP_FP64 ? solve<double>(h, all, info) : solve<float>(h, all, info);
+}
+
+ep_status ep_solve_chunks(ep_handle h, int max_chunks, ep_solve_info *info) {
+  if (!h || max_chunks < 1) return fail(h, EP_ERR_ARG, "ep_solve_chunks: null handle or max_chunks < 1");
+  if (!h->in_increment) return fail(h, EP_ERR_STATE, "ep_solve_chunks: apply an increment first");
+  return h->prec == EP_FP64 ? solve<double>(h, max_chunks, info) : solve<float>(h, max_chunks, info);
 }
 
 ep_status ep_commit_increment(ep_handle h) {
@@ -997,9 +1087,12 @@ ep_status ep_snapshot(ep_handle h) {
   if (!h) return fail(nullptr, EP_ERR_ARG, "null handle");
   auto arr = history_arrays(h);
   const size_t nb = h->g.box * sizeof(double);
-  if (!h->snap) CK(h, cudaMalloc((void **)&h->snap, nb * arr.size()));
+  // plus the last return scale (sweep type), a feature of the warm start
+  const size_t ns = h->g.box * (h->prec == EP_FP64 ? sizeof(double) : sizeof(float));
+  if (!h->snap) CK(h, cudaMalloc((void **)&h->snap, nb * arr.size() + ns));
   for (size_t q = 0; q < arr.size(); ++q)
     CK(h, cudaMemcpyAsync(h->snap + q * nb, arr[q], nb, cudaMemcpyDeviceToDevice, h->stream));
+  CK(h, cudaMemcpyAsync(h->snap + arr.size() * nb, h->s, ns, cudaMemcpyDeviceToDevice, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
   h->snap_started = h->started;
   h->snap_commits = h->n_commits;
@@ -1012,13 +1105,16 @@ ep_status ep_restore(ep_handle h) {
   if (!h->snap) return fail(h, EP_ERR_STATE, "ep_restore: no snapshot taken");
   auto arr = history_arrays(h);
   const size_t nb = h->g.box * sizeof(double);
+  const size_t ns = h->g.box * (h->prec == EP_FP64 ? sizeof(double) : sizeof(float));
   for (size_t q = 0; q < arr.size(); ++q)
     CK(h, cudaMemcpyAsync(arr[q], h->snap + q * nb, nb, cudaMemcpyDeviceToDevice, h->stream));
+  CK(h, cudaMemcpyAsync(h->s, h->snap + arr.size() * nb, ns, cudaMemcpyDeviceToDevice, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
   h->started = h->snap_started;
   h->n_commits = h->snap_commits;
   h->adv_done = h->snap_adv_done;   // a restored history is advected again
   h->in_increment = false;
+  h->solving = false;
   return EP_OK;
 }
 
@@ -1059,6 +1155,7 @@ ep_status ep_time_sweep(ep_handle h, int iters, double *ms_out, int n_out, int *
     if (n_out > 1) ms_out[1] = acc[0] / iters;
     if (n_kernels) *n_kernels = 1;
     h->in_increment = false;
+    h->solving = false;
     return EP_OK;
   }
   const bool fused = h->prec == EP_FP64 ? use_fused<double>(h) : use_fused<float>(h);
@@ -1080,6 +1177,7 @@ ep_status ep_time_sweep(ep_handle h, int iters, double *ms_out, int n_out, int *
     if (n_out > 1) ms_out[1] = acc[0] / iters;
     if (n_kernels) *n_kernels = 1;
     h->in_increment = false;
+    h->solving = false;
     return EP_OK;
   }
   for (int it = 0; it < iters; ++it) {
@@ -1115,6 +1213,7 @@ ep_status ep_time_sweep(ep_handle h, int iters, double *ms_out, int n_out, int *
   for (int q = 0; q < n_out && q <= nk; ++q) ms_out[q] = acc[q] / iters;
   if (n_kernels) *n_kernels = nk;
   h->in_increment = false;  // the sweep state was overwritten
+  h->solving = false;
   return EP_OK;
 }
 
@@ -1296,6 +1395,7 @@ ep_status batch_restart(ep_batch *b) {
   for (int q = 0; q < b->count; ++q) {
     ep_grid *h = b->g[q];
     h->in_increment = false;
+    h->solving = false;
     ep_status r = apply_common(h, h->rate, b->dt, nullptr, nullptr);
     if (r != EP_OK) return bfail(b, r, h->err);
   }
@@ -1453,6 +1553,7 @@ ep_status ep_destroy(ep_handle h) {
   if (h->snap) cudaFree(h->snap);
   if (h->wx) cudaFree(h->wx);   // warm-start network input / output
   if (h->wy) cudaFree(h->wy);
+  if (h->w0) cudaFree(h->w0);
   delete h;
   return EP_OK;
 }

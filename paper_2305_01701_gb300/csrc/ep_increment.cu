@@ -208,94 +208,6 @@ __global__ void k_unpack(const double *src, double *box, int ex, int ey, int ez,
   box[((long long)k * py + j) * px + i] = src[t];
 }
 
-// ---- learned warm start: features, scale, target and start increment ------
-__device__ __forceinline__ void atomic_max_abs(unsigned long long *slot, double v) {
-  unsigned long long b = (unsigned long long)__double_as_longlong(fabs(v));
-  if (b) atomicMax(slot, b);
-}
-
-__global__ void k_warm_scale(Geo g, History H, const double *vp0, const double *vp1, const double *vp2,
-                             unsigned long long *slot) {
-  const Pos3 q = pos3(g);
-  double m = 0.0;
-  if (q.in) {
-    const double *vp[3] = {vp0, vp1, vp2};
-    for (int d = 0; d < g.ndim; ++d)
-      if (face_in(g, d, q.i, q.j, q.k)) m = fmax(m, fabs(H.v[d][q.e] - vp[d][q.e]));
-  }
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) atomic_max_abs(slot, m);
-}
-
-// feature tensor (nd + 2) x Zp x Yp x Xp at cell centres
-template <typename T>
-__global__ void k_warm_features(Geo g, History H, const double *vp0, const double *vp1, const double *vp2,
-                                const T *s_last, double cmax, const unsigned long long *slot, float *x, int Xp,
-                                int Yp, int Zp) {
-  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long nv = (long long)Xp * Yp * Zp;
-  if (t >= nv) return;
-  const int i = (int)(t % Xp), j = (int)((t / Xp) % Yp), k = (int)(t / ((long long)Xp * Yp));
-  const int nd = g.ndim;
-  const bool in = i < g.nx && j < g.ny && k < (nd == 3 ? g.nz : 1);
-  const double S = __longlong_as_double((long long)*slot);
-  const double inv = S > 0.0 ? 1.0 / S : 0.0;
-  const double *vp[3] = {vp0, vp1, vp2};
-  const long long e = in ? g.idx(i, j, k) : 0;
-  const long long off[3] = {1, g.px, g.plane};
-  for (int d = 0; d < nd; ++d) {
-    float v = 0.f;
-    if (in) v = (float)(0.5 * ((H.v[d][e] - vp[d][e]) + (H.v[d][e + off[d]] - vp[d][e + off[d]])) * inv);
-    x[d * nv + t] = v;
-  }
-  x[nd * nv + t] = in ? (float)(1.0 - (double)s_last[e]) : 0.f;
-  x[(nd + 1) * nv + t] = in ? (float)(H.coh[e] / cmax) : 0.f;
-}
-
-__global__ void k_warm_target(Geo g, History H, const double *vp0, const double *vp1, const double *vp2,
-                              const float *feat, double S, float *out, int Xp, int Yp, int Zp) {
-  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long nv = (long long)Xp * Yp * Zp;
-  if (t >= nv) return;
-  const int i = (int)(t % Xp), j = (int)((t / Xp) % Yp), k = (int)(t / ((long long)Xp * Yp));
-  const int nd = g.ndim;
-  const bool in = i < g.nx && j < g.ny && k < (nd == 3 ? g.nz : 1);
-  const double inv = S > 0.0 ? 1.0 / S : 0.0;
-  const double *vp[3] = {vp0, vp1, vp2};
-  const long long e = in ? g.idx(i, j, k) : 0;
-  const long long off[3] = {1, g.px, g.plane};
-  for (int d = 0; d < nd; ++d) {
-    float v = 0.f;
-    if (in) v = (float)(0.5 * ((H.v[d][e] - vp[d][e]) + (H.v[d][e + off[d]] - vp[d][e + off[d]])) * inv) - feat[d * nv + t];
-    out[d * nv + t] = v;
-  }
-}
-
-// start increment at interior faces: dv = (v - vp) + S * (mean of the two
-// adjacent centre predictions)
-__global__ void k_warm_dv(Geo g, History H, const double *vp0, const double *vp1, const double *vp2,
-                          const float *y, const unsigned long long *slot, double *dv0, double *dv1, double *dv2,
-                          int Xp, int Yp, int Zp) {
-  const Pos3 q = pos3(g);
-  if (!q.in) return;
-  const double S = __longlong_as_double((long long)*slot);
-  const double *vp[3] = {vp0, vp1, vp2};
-  double *dv[3] = {dv0, dv1, dv2};
-  const long long nv = (long long)Xp * Yp * Zp;
-  for (int d = 0; d < g.ndim; ++d) {
-    double v = 0.0;
-    if (face_in(g, d, q.i, q.j, q.k) && !face_wall(g, d, q.i, q.j, q.k)) {
-      const int c[3] = {q.i, q.j, q.k};
-      int lo[3] = {c[0], c[1], c[2]};
-      lo[d] -= 1;
-      const long long a = ((long long)c[2] * Yp + c[1]) * Xp + c[0];
-      const long long b = ((long long)lo[2] * Yp + lo[1]) * Xp + lo[0];
-      v = (H.v[d][q.e] - vp[d][q.e]) + S * 0.5 * ((double)y[d * nv + a] + (double)y[d * nv + b]);
-    }
-    dv[d][q.e] = v;
-  }
-}
-
 // ---- advection of the old stress (the v_k d sigma_ij / dx_k term, Eq. j1) ----
 // Once per increment: f <- f - dt * sum_e v_e D_e f for every history
 // component, with H.v the last converged velocity.  D_e is the first-order
@@ -375,33 +287,6 @@ __global__ void k_advect(Geo g, History H, const Scal *sc, double *tn0, double *
 
 }  // namespace
 
-void launch_warm_scale(const Geo &g, const History &H, const double *const vp[3], unsigned long long *slot,
-                       cudaStream_t st) {
-  cudaMemsetAsync(slot, 0, sizeof(unsigned long long), st);
-  k_warm_scale<<<blocks_for(g.box), kThreads, 0, st>>>(g, H, vp[0], vp[1], vp[2], slot);
-}
-template <typename T>
-void launch_warm_features(const Geo &g, const History &H, const double *const vp[3], const T *s_last, double cmax,
-                          const unsigned long long *slot, float *x, const int dims[3], cudaStream_t st) {
-  long long nv = (long long)dims[0] * dims[1] * dims[2];
-  k_warm_features<T><<<blocks_for(nv), kThreads, 0, st>>>(g, H, vp[0], vp[1], vp[2], s_last, cmax, slot, x, dims[0],
-                                                          dims[1], dims[2]);
-}
-template void launch_warm_features<float>(const Geo &, const History &, const double *const[3], const float *, double,
-                                          const unsigned long long *, float *, const int[3], cudaStream_t);
-template void launch_warm_features<double>(const Geo &, const History &, const double *const[3], const double *,
-                                           double, const unsigned long long *, float *, const int[3], cudaStream_t);
-void launch_warm_target(const Geo &g, const History &H, const double *const vp[3], const float *feat, double S,
-                        float *out, const int dims[3], cudaStream_t st) {
-  long long nv = (long long)dims[0] * dims[1] * dims[2];
-  k_warm_target<<<blocks_for(nv), kThreads, 0, st>>>(g, H, vp[0], vp[1], vp[2], feat, S, out, dims[0], dims[1],
-                                                     dims[2]);
-}
-void launch_warm_dv(const Geo &g, const History &H, const double *const vp[3], const float *y,
-                    const unsigned long long *slot, double *const dv[3], const int dims[3], cudaStream_t st) {
-  k_warm_dv<<<blocks_for(g.box), kThreads, 0, st>>>(g, H, vp[0], vp[1], vp[2], y, slot, dv[0], dv[1], dv[2], dims[0],
-                                                    dims[1], dims[2]);
-}
 
 void launch_start_velocity(const Geo &g, const History &H, const double *const dv[3], const Scal *sc,
                            int started, const double L[3], cudaStream_t st) {

@@ -236,15 +236,26 @@ void launch_line_integrals(const Geo &g, const History &H, double *out2, cudaStr
 void launch_advect(const Geo &g, const History &H, const Scal *sc, double *const tn_out[3], double *const ts_out[3],
                    double *p_out, cudaStream_t st);
 void launch_pack(const double *box, double *dst, int ex, int ey, int ez, int px, int py, cudaStream_t st);
-void launch_warm_scale(const Geo &g, const History &H, const double *const vp[3], unsigned long long *slot,
-                       cudaStream_t st);
+// learned warm start (ep_warm.cu): 1 / the scales of the channels
+struct WarmScales {
+  double sv_inv;    // 1 / S_v, S_v = 0.1 |a| L_max
+  double st_inv;    // 1 / S_t, S_t = 2 G |a| dt
+  double se_inv;    // 1 / S_e, S_e = 10 |a| dt
+  double cmax_inv;  // 1 / max c
+};
+__host__ __device__ constexpr int warm_in_channels(int nd) { return nd == 3 ? 13 : 9; }
+__host__ __device__ constexpr int warm_out_channels(int nd) { return nd == 3 ? 9 : 5; }
 template <typename T>
-void launch_warm_features(const Geo &g, const History &H, const double *const vp[3], const T *s_last, double cmax,
-                          const unsigned long long *slot, float *x, const int dims[3], cudaStream_t st);
-void launch_warm_target(const Geo &g, const History &H, const double *const vp[3], const float *feat, double S,
-                        float *out, const int dims[3], cudaStream_t st);
-void launch_warm_dv(const Geo &g, const History &H, const double *const vp[3], const float *y,
-                    const unsigned long long *slot, double *const dv[3], const int dims[3], cudaStream_t st);
+void launch_warm_features(const Geo &g, const History &H, const double *const vp[3], const T *s_last,
+                          const WarmScales &ws, int f, float *x, const int dims[3], cudaStream_t st);
+void launch_warm_target(const Geo &g, const History &H, const double *const vp[3], const float *w0,
+                        const WarmScales &ws, int f, float *out, const int dims[3], cudaStream_t st);
+void launch_warm_record(const Geo &g, const double *const n[3], const double *const s[3], float *w0,
+                        cudaStream_t st);
+void launch_warm_dv(const Geo &g, const float *y, int f, double sv, double *const dv[3], const int dims[3],
+                    cudaStream_t st);
+void launch_warm_stress(const Geo &g, const float *y, int f, double stress_scale, double *const n[3],
+                        double *const s[3], const int dims[3], cudaStream_t st);
 void launch_unpack(const double *src, double *box, int ex, int ey, int ez, int px, int py, cudaStream_t st);
 
 }  // namespace ep

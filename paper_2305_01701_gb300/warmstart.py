@@ -1,65 +1,68 @@
 """Learned warm start: data from the solver's own trajectories, training on
 the GPU with the library's network kernels, and use in later solves.
 
-Each sample is one increment n >= 3 of a plain-start solve.  The features
-(computed by the library before the increment) are the previous increment's
-velocity change at cell centres over its L-infinity norm S, 1 - s and
-c / max(c).  The target (computed after the solve) is this increment's
-velocity change over S minus the previous one.  So the network learns a
-correction to "repeat the last increment", and a zero network reproduces
-that extrapolation.  PyTorch only supplies the device buffers the library
-writes into; every arithmetic step of collection, training and inference
-runs in the library (`zero_loss` reduces the stored targets with torch, for
-the report only).
+Each sample is one increment n >= 3 of a plain-start solve.  The features,
+computed by the library before the increment, describe the previous
+increment's velocity change and the state it left (old stress and pressure
+over the cohesion, the last return scale, the cohesion, the plastic strain);
+the target, computed after the solve, is this increment's velocity change and
+the relaxed-return part of its converged stress state (include/ep.h,
+ep_warm_features / ep_warm_target).  A network that outputs zero reproduces
+the plain start.  PyTorch only supplies the device buffers the library writes
+into; every arithmetic step of collection, training and inference runs in the
+library (`zero_loss` reduces the stored targets with torch, for the report
+only).
 """
 from __future__ import annotations
 
 import numpy as np
 
-from ._native import LOAD_XY, LOAD_XZ, Net
+from ._native import LOAD_XY, LOAD_XZ, Net, warm_in, warm_out  # noqa: F401
 
 
 def new_net(ndim, base=32, levels=3, seed=0, stream=None):
-    """A warm-start network for ndim-dimensional grids (ndim + 2 inputs)."""
-    return Net(ndim, ndim + 2, ndim, base=base, levels=levels, seed=seed, stream=stream)
+    """A warm-start network for ndim-dimensional grids."""
+    return Net(ndim, warm_in(ndim), warm_out(ndim), base=base, levels=levels, seed=seed, stream=stream)
 
 
 class Samples:
-    """Features and targets of one padded grid size, in device buffers."""
+    """Features and targets of one padded size, in device buffers."""
 
     def __init__(self, ndim, dims, capacity, device="cuda"):
         import torch
         self.ndim, self.dims = ndim, tuple(dims)
         nv = int(np.prod([d for d in dims[:ndim]]))
         self.nv = nv
-        self.x = torch.zeros((capacity, ndim + 2, nv), dtype=torch.float32, device=device)
-        self.t = torch.zeros((capacity, ndim, nv), dtype=torch.float32, device=device)
+        self.cin, self.cout = warm_in(ndim), warm_out(ndim)
+        self.x = torch.zeros((capacity, self.cin, nv), dtype=torch.float32, device=device)
+        self.t = torch.zeros((capacity, self.cout, nv), dtype=torch.float32, device=device)
         torch.cuda.synchronize()   # zeroed before the library writes on its own stream
         self.n = 0
 
     def ptr_x(self, i):
-        return self.x.data_ptr() + i * (self.ndim + 2) * self.nv * 4
+        return self.x.data_ptr() + i * self.cin * self.nv * 4
 
     def ptr_t(self, i):
-        return self.t.data_ptr() + i * self.ndim * self.nv * 4
+        return self.t.data_ptr() + i * self.cout * self.nv * 4
 
 
-def collect(grid, a, dt, increments, samples, load_plane=LOAD_XY, warm=False):
+def collect(grid, a, dt, increments, samples, load_plane=LOAD_XY, coarsen=1, warm=False):
     """Solve `increments` increments on `grid` (plain start, or the attached
     network when warm) and store one sample per increment from the third on.
     Returns the iteration count of each increment."""
+    grid.warm_record(True)
     iters = []
     for inc in range(1, increments + 1):
         have = inc >= 3 and samples is not None and samples.n < samples.x.shape[0]
-        scale = None
         if have:
-            scale = grid.warm_features(samples.ptr_x(samples.n))
+            grid.warm_features(samples.ptr_x(samples.n), coarsen)
         grid.apply_increment(a, dt, load_plane, use_warm_start=bool(warm and inc >= 3))
         info = grid.solve_increment()
         iters.append(info["iters"])
         if have:
-            grid.warm_target(samples.ptr_x(samples.n), scale, samples.ptr_t(samples.n))
+            grid.warm_target(samples.ptr_t(samples.n), coarsen)
             samples.n += 1
+    grid.warm_record(False)
     return iters
 
 
@@ -91,8 +94,8 @@ def evaluate(net, groups, batch=2):
 
 
 def zero_loss(groups):
-    """The same mean MSE for a network that outputs zero, i.e. for plain
-    extrapolation of the last increment (the warm start's fallback)."""
+    """The same mean MSE for a network that outputs zero, i.e. for the plain
+    start (the warm start's fallback)."""
     total, count = 0.0, 0
     for g in groups:
         if g.n:

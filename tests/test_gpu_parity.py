@@ -275,6 +275,47 @@ def test_fp32_warp_strips_many_strips_and_segments_against_oracle(P, tile):
     assert worst["epl_max"] > 0
 
 
+@pytest.mark.parametrize("nd,prec", [(2, "fp64"), (3, "fp32")])
+def test_solve_in_chunks_equals_one_solve(P, nd, prec):
+    """ep_solve_chunks(1) called until the solve is decided performs the same
+    iterations as one ep_solve_increment: same check iteration, same frozen
+    point, fields bit for bit; PENDING is returned while undecided and a new
+    increment abandons an undecided solve."""
+    if nd == 2:
+        s = E.config(1, n=(40, 34), tol=1e-9)
+    else:
+        s = E.config(3, n=(20, 17, 14), inclusion_radius=0.2)
+    precision = P.FP64 if prec == "fp64" else P.FP32_MIXED
+    fields = FIELDS_2D if nd == 2 else FIELDS_3D
+    nchk = 20 if nd == 2 else 100
+    ga = gpu_grid(P, s, precision, n_chk=nchk, freeze_iter=200 if nd == 3 else 0)
+    gb = gpu_grid(P, s, precision, n_chk=nchk, freeze_iter=200 if nd == 3 else 0)
+    pending = 0
+    for inc in range(1, 8):
+        ga.apply_increment_rates(rates_of(s), s.dt)
+        ia = ga.solve_increment()
+        gb.apply_increment_rates(rates_of(s), s.dt)
+        while True:
+            ib = gb.solve_chunks(1)
+            if ib["status"] != P.PENDING:
+                break
+            pending += 1
+            assert ib["iters"] % nchk == 0
+        assert ib["status"] == 0 and ib["iters"] == ia["iters"] and ib["frozen_at"] == ia["frozen_at"]
+        for f in fields:
+            assert np.array_equal(ga.get(f), gb.get(f)), (inc, f)
+    assert pending > 0 and ia["n_plastic"] > 0
+    # an undecided solve is abandoned by the next increment
+    gb.apply_increment_rates(rates_of(s), s.dt)
+    assert gb.solve_chunks(1)["status"] == P.PENDING
+    ga.apply_increment_rates(rates_of(s), s.dt)
+    gb.apply_increment_rates(rates_of(s), s.dt)
+    ia, ib = ga.solve_increment(), gb.solve_increment()
+    assert ia["iters"] == ib["iters"]
+    ga.close()
+    gb.close()
+
+
 def test_advection_fp64_parity_2d(P):
     """Advection of the old stress (Eq. j1) on: every increment after the
     first transports tau_hat and p_hat with the last converged velocity.
