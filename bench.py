@@ -1,25 +1,30 @@
 #!/usr/bin/env python3
 """Benchmark of the pseudo-transient elasto-plastic solve on GB300.
 
-Workload (default): the 3D elasto-plastic box of 127^3 cells under x-z pure
-shear with a spherical weak inclusion (radius 0.05, half cohesion) and +-1%
-seeded cohesion noise; K = 2, G = 1, c = 1.5e-3 G, phi = 30 deg, strain
-increment 1e-4, tolerance 1e-6; FP32 sweeps with FP64 norms, convergence
-test and history.  One step is one load increment solved to tolerance
-(start state, pseudo-transient sweeps, FP64 commit): the first increment at
-which the inclusion yields (increment 5), re-solved from a device checkpoint
-each step so that every step does the same work.  The same increment is
-then solved once with plain FP64 sweeps ("fp64_plain").
+Workload (default): the 3D elasto-plastic box of 511^3 cells (133 M cells)
+under x-z pure shear with a spherical weak inclusion (radius 0.05, half
+cohesion) and +-1 % seeded cohesion noise; K = 2, G = 1, c = 1.5e-3 G,
+phi = 30 deg, strain increment 1e-4, tolerance 1e-6, residual check every
+1000 iterations, frozen plasticity after 16 n_x iterations (Sec. 3.3); FP32
+sweeps with FP64 norms, convergence test and history.
 
---size 511 runs the 511^3 box of the same setup.  Its first plastic
-increment takes about 13,000 iterations with frozen plasticity (about 90 s in
-FP32 and 12 minutes in FP64), so it is not the default step.
+Learned warm start: a 3-level 3D U-Net (base 32, BF16 weights, FP32
+accumulation) is trained on the GPU with the library's kernels on the
+trajectories of 127^3 boxes of the same setup (other seeds and cohesions),
+on coarse cells of 1/64 of the box (2^3 fine cells there, 8^3 here).
 
-Metric: effective HBM throughput of the sweeps (algorithmic bytes per cell
-per iteration x cells x iterations / device time) and the wall time per
-increment.  With --gpus N (torchrun), each rank solves its own replica (the
-solve does not shard: no data-path collective) and value is the sum over
-ranks divided by the slowest rank's time.
+Steps: the increment sequence from the first plastic increment (5) on, one
+chunk of 1000 sweeps per step; the step that needs a new increment starts it
+(warm-start inference and start state), the step whose check converges
+commits it.  value = algorithmic sweep bytes of the timed steps / their
+device time.  Then the timed increment is solved whole from a device
+checkpoint with the warm start (end to end through the C ABI with host
+buffers: `e2e`) and with the plain start, and once more with plain FP64
+sweeps on an FP64 box ("per_increment": wall time and GB/s of each).
+
+With --gpus N (torchrun), each rank solves its own replica (the solve does
+not shard: no data-path collective) and value is the sum over ranks divided
+by the slowest rank's time.  --size selects a smaller box of the same setup.
 
 --impl reference times the FP64 CPU oracle on the host cores on a bounded
 sample of the same workload (a smaller grid of the same setup).
@@ -43,17 +48,19 @@ METRIC = "HBM GB/s and wall time per increment to tol 1e-6: warm-start FP32 vs p
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--size", type=int, default=127, help="cells per side of the 3D box")
-    ap.add_argument("--increment", type=int, default=5, help="load increment that is timed")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
-    ap.add_argument("--no-fp64", action="store_true", help="skip timing the plain FP64 solve")
-    ap.add_argument("--warm", action="store_true", help="also train the warm-start network and time a warm increment")
-    ap.add_argument("--warm-increment", type=int, default=7, help="increment timed with and without the warm start")
-    ap.add_argument("--warm-train", type=int, default=2, help="held-out setups whose trajectories train the network")
-    ap.add_argument("--warm-steps", type=int, default=150, help="training steps")
+    ap.add_argument("--size", type=int, default=511, help="cells per side of the 3D box")
+    ap.add_argument("--increment", type=int, default=5, help="first increment of the timed sequence")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 increment")
+    ap.add_argument("--no-warm", action="store_true", help="plain start instead of the learned warm start")
+    ap.add_argument("--coarsen", type=int, default=0,
+                    help="fine cells per coarse cell side of the network's grid (0: size / 64)")
+    ap.add_argument("--train-size", type=int, default=127, help="box of the training trajectories")
+    ap.add_argument("--warm-train", type=int, default=3, help="setups whose trajectories train the network")
+    ap.add_argument("--warm-incs", type=int, default=4, help="increments after the first plastic one per setup")
+    ap.add_argument("--warm-steps", type=int, default=300, help="training steps")
     ap.add_argument("--warm-base", type=int, default=32, help="base channels of the network")
     ap.add_argument("--batch", type=int, default=0, help="time the batched 2D solve of this many instances")
     ap.add_argument("--batch-increment", type=int, default=3, help="batched increment that is timed")
@@ -63,12 +70,17 @@ def parse():
     ap.add_argument("--batch-nchk", type=int, default=1000,
                     help="check interval of the batched FP32 solve (the FP32 stopping test needs long intervals)")
     ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--oracle-plan", action="store_true", help="time the CPU oracle per iteration and increment")
+    ap.add_argument("--symmetry-study", action="store_true", help="the paper's large vs small increment study")
+    ap.add_argument("--sym-strain", type=float, default=1.4e-3, help="total strain of the symmetry study")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-size", type=int, default=24)
-    ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--kernel", default="auto", choices=sorted(["auto", "staged", "fused", "tma", "reg"]),
                     help="sweep kernel: auto (library default), staged, fused (cp.async), tma or reg")
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.coarsen <= 0:
+        a.coarsen = max(1, round(a.size / 64))
+    return a
 
 
 def dist_env():
@@ -169,6 +181,114 @@ def oracle_increment_rate(size, tol, increment, max_seconds=30.0):
     return sum(times) / len(times), iters, size ** 3
 
 
+def oracle_plan(args):
+    """The CPU baseline plan: the FP64 oracle, single-threaded as it stands,
+    timed per iteration at 64^2, 511^2, 63^3 and 127^3 (a perturbed start
+    velocity keeps it iterating; a fixed count of iterations) and over whole
+    increments at 64^2 (config 1, increments 1-12) and 63^3 (increments 1-5,
+    the last the first plastic one), with the host's core count and CPU
+    model.  Prints one JSON object."""
+    import platform
+    import numpy as np
+    import ep_inputs as E
+    import oracle as O
+
+    def cpu_model():
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+            out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+            for line in out.splitlines():
+                if line.startswith("Model name"):
+                    return line.split(":", 1)[1].strip()
+        except Exception:
+            pass
+        return platform.processor() or "unknown"
+
+    res = {"host": {"nproc": os.cpu_count(), "cpu_model": cpu_model(), "machine": platform.machine(),
+                    "threads_used": 1}, "per_iteration": [], "increments": []}
+    for nd, n, iters in ((2, 64, 500), (2, 511, 60), (3, 63, 60), (3, 127, 12)):
+        s = E.config(1 if nd == 2 else 3, n=(n,) * nd, tol=1e-30)
+        o = O.from_setup(s, max_iter=iters, n_chk=iters)
+        rates = [s.a, -s.a] if nd == 2 else [s.a, 0.0, -s.a]
+        o.apply_increment(rates, s.dt)
+        rng = np.random.default_rng(0)
+        v = np.concatenate([o.get(c).ravel() for c in ("v0x", "v0y", "v0z")[:nd]])
+        o.set_start(v * (1.0 + 1e-3 * rng.standard_normal(v.size)))
+        t0 = time.perf_counter()
+        info = o.solve_increment(commit=False, raise_on_fail=False)
+        dt = time.perf_counter() - t0
+        cells = n ** nd
+        k = max(info["iters"], 1)
+        res["per_iteration"].append({"grid": "%d^%d" % (n, nd), "iterations": k, "ms_per_iteration": dt / k * 1e3,
+                                     "ns_per_cell_iteration": dt / k / cells * 1e9,
+                                     "GB_per_s_algorithmic": alg_bytes_per_cell(nd, "fp64") * cells * k / dt / 1e9})
+    for nd, n, incs in ((2, 64, 12), (3, 63, 5)):
+        s = E.config(1 if nd == 2 else 3, n=(n,) * nd, tol=1e-8 if nd == 2 else 1e-6)
+        o = O.from_setup(s)
+        rates = [s.a, -s.a] if nd == 2 else [s.a, 0.0, -s.a]
+        rows = []
+        for inc in range(1, incs + 1):
+            t0 = time.perf_counter()
+            o.apply_increment(rates, s.dt)
+            info = o.solve_increment()
+            rows.append({"increment": inc, "iterations": info["iters"], "seconds": time.perf_counter() - t0,
+                         "n_plastic": info["n_plastic"]})
+        res["increments"].append({"grid": "%d^%d" % (n, nd), "tol": s.tol, "rows": rows,
+                                  "seconds_total": sum(r["seconds"] for r in rows)})
+    print(json.dumps(res))
+    return 0
+
+
+def symmetry_study(args):
+    """The paper's symmetry study (Sec. 4.3) on the GPU: the 383 x 191 box
+    with a central pressure anomaly (no Jaumann term, elastic limit), loaded
+    to the same total strain once in 7 large increments and once in 180
+    small ones, FP64 sweeps (warp strips) to tolerance --tol at every
+    increment.  Prints, per run, the iterations and the integrated sigma_xx
+    on the centre line per increment, and the mirror asymmetry of the final
+    accumulated-strain invariant eps_II: |E - E mirrored| / |E| (L2) across
+    the vertical and horizontal centre lines and through the centre."""
+    import numpy as np
+    import torch
+    import ep_inputs as E
+    import paper_2305_01701_gb300 as P
+    torch.cuda.set_device(0)
+    total = args.sym_strain
+    out = {"box": "383 x 191 (L = 2 x 1), c = 2e-3, mu_s = 1e6, no Jaumann term, p = c/2 within 0.05 of the centre",
+           "total_strain": total, "tol": args.tol, "runs": []}
+    for incs in (7, 180):
+        s = E.anomaly_setup()
+        dt = total / incs
+        g = P.Grid(2, s.n, s.L, precision=P.FP64)
+        g.set_material(s.K, s.G, s.mu_s, s.phi_deg, s.psi_deg, s.cohesion())
+        g.set_solver(tol=args.tol, max_iter=10000000, n_chk=100, jaumann=False, freeze_iter=0)
+        g.set_kernel(P.KERNEL_FUSED, 3)
+        g.set("p", E.pressure_anomaly(s.n, s.L[:2], s.extra["pressure_anomaly"]["value"],
+                                     s.extra["pressure_anomaly"]["radius"]))
+        rows = []
+        t0 = time.perf_counter()
+        for inc in range(1, incs + 1):
+            g.apply_increment(s.a, dt, P.LOAD_XY)
+            info = g.solve_increment()
+            rows.append([inc, info["iters"], info["sxx_int_centre"], info["n_plastic"]])
+        wall = time.perf_counter() - t0
+        e = g.get("eii")
+        nrm = float(np.sqrt((e ** 2).sum()))
+        asym = {"x_mirror": float(np.sqrt(((e - e[:, ::-1]) ** 2).sum())) / nrm,
+                "y_mirror": float(np.sqrt(((e - e[::-1, :]) ** 2).sum())) / nrm,
+                "point": float(np.sqrt(((e - e[::-1, ::-1]) ** 2).sum())) / nrm}
+        hot = e > 0.5 * e.max()
+        out["runs"].append({"increments": incs, "dt": dt, "wall_s": wall, "asymmetry": asym,
+                            "band_cells_left_right": [int(hot[:, : s.n[0] // 2].sum()), int(hot[:, s.n[0] // 2:].sum())],
+                            "band_cells_bottom_top": [int(hot[: s.n[1] // 2].sum()), int(hot[s.n[1] // 2:].sum())],
+                            "eii_max": float(e.max()), "rows": rows})
+        g.close()
+    print(json.dumps(out))
+    return 0
+
+
 def alg_bytes_per_cell(ndim, precision):
     """Bytes one fused sweep iteration must move per cell: it reads the
     velocity increment, the stress state and pressure, the base trial and
@@ -216,32 +336,24 @@ def reference_arm(args):
 KERNEL = {"auto": -1, "staged": 0, "fused": 1, "tma": 2, "reg": 3}
 
 
-def one_step(P, g, s):
-    """One pass of the path: back to the checkpoint before the timed
-    increment, start it, iterate to tolerance, commit."""
-    g.restore()
-    g.apply_increment(s.a, s.dt, P.LOAD_XZ)
-    return g.solve_increment()
-
-
 def check_interval(size, precision):
     """Check every 100 iterations, or every 1000 for FP32 boxes above 200^3:
     the FP32 stopping measure needs the longer interval there."""
     return 1000 if precision == "fp32" and size > 200 else 100
 
 
-def make_grid(P, s, precision, kernel="auto", stream=None):
+def make_grid(P, s, precision, kernel="auto", stream=None, nchk=None):
     g = P.Grid(3, s.n, s.L, precision=P.FP64 if precision == "fp64" else P.FP32_MIXED, stream=stream)
     g.set_kernel(KERNEL[kernel], -1)
     g.set_material(s.K, s.G, s.mu_s, s.phi_deg, s.psi_deg, s.cohesion())
-    g.set_solver(tol=s.tol, max_iter=2000000, n_chk=check_interval(s.n[0], precision))
+    g.set_solver(tol=s.tol, max_iter=2000000, n_chk=nchk or check_interval(s.n[0], precision))
     return g
 
 
-def prepare(P, s, precision, increment, kernel="auto", stream=None):
+def prepare(P, s, precision, increment, kernel="auto", stream=None, nchk=None):
     """Solve the increments before the timed one, then checkpoint the
-    history on the device (every step restarts from it)."""
-    g = make_grid(P, s, precision, kernel, stream)
+    history on the device (every whole-increment solve restarts from it)."""
+    g = make_grid(P, s, precision, kernel, stream, nchk)
     for inc in range(1, increment):
         g.apply_increment(s.a, s.dt, P.LOAD_XZ)
         g.solve_increment()
@@ -262,29 +374,109 @@ def aggregate(torch, dist, seconds, units, device):
     return float(tmax.item()), float(tot.item())
 
 
-def timed_steps(torch, P, g, s, stream, steps, barrier):
-    """Run `steps` steps between CUDA events on the library's stream (with a
-    barrier and a device synchronisation on both sides); returns (device
-    seconds, solve infos)."""
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier()
-    ev0.record(stream)
-    infos = [one_step(P, g, s) for _ in range(steps)]
-    ev1.record(stream)
-    barrier()
-    return ev0.elapsed_time(ev1) * 1e-3, infos
-
-
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # dominant kernel from one ncu capture of the benchmark command, by kernel and
 # box size; the entry must be dropped when the kernel changes.
 NCU_TRAFFIC = {("k_fused3d_reg", 127): 271.8e6}
+NCU_SOURCE = {("k_fused3d_reg", 127): "ncu --set full capture of one launch at 127^3 (profiles/)"}
+# the survey's algorithmic bytes per cell of a 3D FP32 sweep whose stress is
+# no pseudo-time state (reported beside the fraction by the scheme's bytes)
+SURVEY_BYTES_3D_FP32 = 80.0
 
 
 def kernel_names(ktimes, kernel):
     if len(ktimes) == 2:
         return [{"tma": "k_fused3d_tma", "reg": "k_fused3d_reg", "fused": "k_fused3d"}.get(kernel, "k_fused3d_reg")]
     return ["k_strain", "k_trial", "k_return_centres", "k_return_edges", "k_velocity"]
+
+
+class Walk:
+    """Steps through the increment sequence one chunk at a time: a step
+    applies a new increment when none is open (with the warm start when a
+    network is attached) and runs one chunk of n_chk sweeps of the open
+    increment's iteration (ep_solve_chunks)."""
+
+    def __init__(self, P, g, s, warm):
+        self.P, self.g, self.s, self.warm = P, g, s, warm
+        self.open, self.done, self.finished = False, 0, []
+
+    def step(self):
+        """Returns the sweeps this step performed."""
+        P, g, s = self.P, self.g, self.s
+        if not self.open:
+            g.apply_increment(s.a, s.dt, P.LOAD_XZ, use_warm_start=self.warm)
+            self.open, self.done = True, 0
+        info = g.solve_chunks(1)
+        if info["status"] == P.PENDING:
+            n = info["iters"] - self.done
+            self.done = info["iters"]
+            return n
+        self.open = False
+        self.finished.append(info)
+        return info["iters"] + 1 - self.done
+
+
+def train_warm(args, torch, P, stream):
+    """The learned warm start for the benchmark box: a 3-level 3D U-Net (BF16
+    weights, FP32 accumulation) trained on the GPU with the library's kernels
+    on trajectories of smaller boxes of the same setup (other seeds and
+    cohesions), on coarse cells of the same physical size as the benchmark
+    box's coarse cells."""
+    import ep_inputs as E
+    from paper_2305_01701_gb300 import warmstart as W
+    t0 = time.perf_counter()
+    n_tr = args.train_size
+    f_tr = max(1, round(args.coarsen * n_tr / args.size))
+    net = W.new_net(3, base=args.warm_base, levels=3, seed=7, stream=stream.cuda_stream)
+    incs = args.increment + args.warm_incs
+    ref = E.config(5, n=(n_tr,) * 3, tol=args.tol)
+    dims = None
+    groups = []
+    iters = []
+    for q in range(args.warm_train):
+        ts = E.config(5, n=(n_tr,) * 3, tol=args.tol, seed=ref.seed + 101 + q, c0=ref.c0 * (1.0 + 0.04 * q))
+        gt = make_grid(P, ts, "fp32", args.kernel, stream.cuda_stream)
+        dims = gt.warm_dims(f_tr)
+        data = W.Samples(3, dims, capacity=incs)
+        iters.append(W.collect(gt, ts.a, ts.dt, incs, data, load_plane=P.LOAD_XZ, coarsen=f_tr))
+        gt.close()
+        groups.append(data)
+    zero = W.zero_loss(groups)
+    before = W.evaluate(net, groups)
+    W.train(net, groups, steps=args.warm_steps, lr=1e-3, batch=2)
+    torch.cuda.synchronize()
+    after = W.evaluate(net, groups)
+    info = {"net": "3-level U-Net, base %d, BF16 weights, FP32 accumulation" % args.warm_base,
+            "train_box": "%d^3, coarse cells of %d^3 fine cells (%s per side)" % (n_tr, f_tr, "x".join(map(str, dims[:3]))),
+            "setups": args.warm_train, "samples": sum(d.n for d in groups), "steps": args.warm_steps,
+            "train_mse_before": before, "train_mse_after": after, "train_mse_zero_net": zero,
+            "train_iterations": iters, "seconds": time.perf_counter() - t0}
+    return net, info
+
+
+def full_increment(torch, P, g, s, stream, barrier, warm, host=None):
+    """Solve the checkpointed increment to tolerance from the checkpoint;
+    device time by CUDA events on the grid's stream.  With host buffers the
+    same solve runs end to end: the FP64 history uploaded from pinned host
+    memory first, the converged fields read back to it last, all inside the
+    wall-clock region."""
+    g.restore()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    t0 = time.perf_counter()
+    if host is not None:
+        for f, b in host["in"].items():
+            g.set_from(f, b.data_ptr(), b.numel())
+    ev0.record(stream)
+    g.apply_increment(s.a, s.dt, P.LOAD_XZ, use_warm_start=warm)
+    info = g.solve_increment()
+    ev1.record(stream)
+    if host is not None:
+        for f, b in host["out"].items():
+            g.get_into(f, b.data_ptr(), b.numel())
+    barrier()
+    wall = time.perf_counter() - t0
+    return ev0.elapsed_time(ev1), wall, info
 
 
 def our_arm(args):
@@ -306,64 +498,84 @@ def our_arm(args):
     stream = torch.cuda.Stream()
     s = setup_for(args.size, args.tol)
     cells = s.n[0] * s.n[1] * s.n[2]
-    g = prepare(P, s, args.precision, args.increment, args.kernel, stream.cuda_stream)
-    for _ in range(args.warmup):           # full passes of the timed step
-        one_step(P, g, s)
+    nchk = check_interval(s.n[0], "fp32")
+    net, training = (None, None) if args.no_warm else train_warm(args, torch, P, stream)
+
+    # the benchmark box: the increments before the timed one, then a checkpoint
+    g = prepare(P, s, "fp32", args.increment, args.kernel, stream.cuda_stream)
+    if net is not None:
+        g.attach_warm_start(net, args.coarsen)
     bpc = g.sweep_bytes_per_cell()
-    nchk = check_interval(s.n[0], args.precision)
+    walk = Walk(P, g, s, warm=net is not None)
+    for _ in range(args.warmup):
+        walk.step()
     clk = Clocks(local)
     clk.start()
-    sec, infos = timed_steps(torch, P, g, s, stream, args.steps, barrier)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0.record(stream)
+    sweeps = [walk.step() for _ in range(args.steps)]
+    ev1.record(stream)
+    barrier()
     clocks = clk.stop()
-    iters = sum(i["iters"] for i in infos)
-    tmax, total_bytes = aggregate(torch, dist, sec, bpc * cells * iters, "cuda")
+    sec = ev0.elapsed_time(ev1) * 1e-3
+    tmax, total_bytes = aggregate(torch, dist, sec, bpc * cells * sum(sweeps), "cuda")
     gbs = total_bytes / tmax / 1e9
     ms_per_step = tmax / args.steps * 1e3
 
+    # the timed increment solved whole from the checkpoint: warm start end to
+    # end through the C ABI with host buffers, and the plain start
+    fields_in = ["vx", "vy", "vz", "txx", "tyy", "tzz", "txy", "txz", "tyz", "p", "epl",
+                 "ux", "uy", "uz", "exx", "eyy", "ezz", "exy", "exz", "eyz"]
+    fields_out = ["vx", "vy", "vz", "txx", "tyy", "tzz", "txy", "txz", "tyz", "p", "epl"]
+    g.restore()
+    host = {"in": {}, "out": {}}
+    for f in fields_in:
+        b = torch.empty(g.count(f), dtype=torch.float64, pin_memory=True)
+        g.get_into(f, b.data_ptr(), b.numel())
+        host["in"][f] = b
+    for f in fields_out:
+        host["out"][f] = torch.empty(g.count(f), dtype=torch.float64, pin_memory=True)
+    h2d = sum(b.numel() * 8 for b in host["in"].values()) + 8 * 4
+    d2h = sum(b.numel() * 8 for b in host["out"].values())
+    arms = {}
+    for name, warm in (("warm_fp32", net is not None), ("plain_fp32", False)):
+        if name == "warm_fp32" and net is None:
+            continue
+        dev_ms, wall, info = full_increment(torch, P, g, s, stream, barrier, warm,
+                                            host if name == "warm_fp32" else None)
+        arms[name] = {"ms_per_increment": dev_ms, "iterations": info["iters"], "frozen_at": info["frozen_at"],
+                      "GB_per_s": bpc * cells * (info["iters"] + 1) / (dev_ms * 1e-3) / 1e9, "wall_ms": wall * 1e3}
+    e2e = None
+    if "warm_fp32" in arms:
+        w = arms["warm_fp32"]
+        e2e = {"value": bpc * cells * (w["iterations"] + 1) * world / (w["wall_ms"] * 1e-3) / 1e9, "unit": "GB/s",
+               "ms_per_step": w["wall_ms"], "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "step": "one warm-start increment through the C ABI: FP64 history from pinned host memory, "
+                       "start, solve to tolerance, converged fields back to pinned host memory"}
+
     # dominant sweep kernel: CUDA events on the library's stream around a
-    # burst of back-to-back launches on the same increment
-    ktimes = g.time_sweep(20)
+    # burst of launches on the open timed increment
+    g.restore()
+    g.apply_increment(s.a, s.dt, P.LOAD_XZ)
+    ktimes = g.time_sweep(10 if s.n[0] > 300 else 20)
     kernels = kernel_names(ktimes, args.kernel)
     it_ms = ktimes[-1]
     dom = int(max(range(len(kernels)), key=lambda q: ktimes[q]))
-
-    # end to end through the C ABI with host buffers: the step's inputs (load
-    # rates, time step) in, the converged fields out to pinned host memory
-    e2e = None
-    if args.e2e_steps > 0:
-        fields = ["vx", "vy", "vz", "txx", "tyy", "tzz", "txy", "txz", "tyz", "p", "epl"]
-        bufs = {f: torch.empty(g.count(f), dtype=torch.float64, pin_memory=True) for f in fields}
-        d2h = sum(b.numel() * 8 for b in bufs.values())
-        h2d = 8 * 3 + 8
-        barrier()
-        t0 = time.perf_counter()
-        e_iters = 0
-        for _ in range(args.e2e_steps):
-            e_iters += one_step(P, g, s)["iters"]
-            for f in fields:
-                g.get_into(f, bufs[f].data_ptr(), bufs[f].numel())
-        barrier()
-        et = time.perf_counter() - t0
-        e2e = {"value": bpc * cells * e_iters * world / et / 1e9, "unit": "GB/s",
-               "ms_per_step": et / args.e2e_steps * 1e3, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+    g.close()
+    if net is not None:
+        net.close()
 
     fp64 = None
     if not args.no_fp64:
-        g.close()
-        g64 = prepare(P, s, "fp64", args.increment, "auto", stream.cuda_stream)
-        one_step(P, g64, s)
-        t64, i64 = timed_steps(torch, P, g64, s, stream, 1, barrier)
-        i64 = i64[0]
-        fp64 = {"ms_per_increment": t64 * 1e3, "iterations": i64["iters"], "kernel": "staged",
-                "GB_per_s": g64.sweep_bytes_per_cell() * cells * i64["iters"] / t64 / 1e9,
-                "fp32_speedup": t64 * 1e3 / ms_per_step}
+        g64 = prepare(P, s, "fp64", args.increment, "auto", stream.cuda_stream, nchk=nchk)
+        dev_ms, _, i64 = full_increment(torch, P, g64, s, stream, barrier, False)
+        fp64 = {"ms_per_increment": dev_ms, "iterations": i64["iters"], "frozen_at": i64["frozen_at"],
+                "kernel": "staged",
+                "GB_per_s": g64.sweep_bytes_per_cell() * cells * (i64["iters"] + 1) / (dev_ms * 1e-3) / 1e9}
+        for name in arms:
+            arms[name]["speedup_vs_fp64"] = dev_ms / arms[name]["ms_per_increment"]
         g64.close()
-
-    warm = None
-    if args.warm:
-        warm = warm_arm(args, torch, P, stream, barrier, s, cells)
-        if fp64 is not None and args.warm_increment == args.increment:
-            warm["fp64_plain_ms"] = fp64["ms_per_increment"]
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -384,32 +596,34 @@ def our_arm(args):
             "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
             "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6800 GB/s",
             "traffic": NCU_TRAFFIC.get((kernels[dom], s.n[0])),
-            "traffic_source": "ncu --set full capture of one launch of this command (profiles/)"
-                              if (kernels[dom], s.n[0]) in NCU_TRAFFIC else None,
+            "traffic_source": NCU_SOURCE.get((kernels[dom], s.n[0])),
             "kernel_ms": {k: float(ktimes[q]) for q, k in enumerate(kernels)},
-            "dominant": kernels[dom], "iteration_ms": float(it_ms), "alg_bytes_per_cell": bpc}
+            "dominant": kernels[dom], "iteration_ms": float(it_ms), "alg_bytes_per_cell": bpc,
+            "frac_survey_bytes": SURVEY_BYTES_3D_FP32 * cells / (it_ms * 1e-3) / 1e9 / hbm}
+    warm_desc = "warm start (3D U-Net on coarse cells of %d^3)" % args.coarsen if net is not None else "plain start"
     line = {
         "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
-        "config": {"workload": "3d-ep-xz-inclusion %d^3, increment %d, tol %g, %s sweeps, plain start"
-                   % (s.n[0], args.increment, args.tol, args.precision),
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "3d-ep-xz-inclusion %d^3 (%d cells), increments from %d on, tol %g, fp32 sweeps, %s"
+                   % (s.n[0], cells, args.increment, args.tol, warm_desc),
+                   "step": "one chunk of %d pseudo-transient sweeps of the increment sequence (a new increment, "
+                           "with its warm-start inference and start state, is opened by the step that needs it; "
+                           "a converged one is committed by the step that decides it)" % nchk,
                    "sweep_kernel": kernels[0] if len(kernels) == 1 else "staged",
-                   "cells": cells, "iterations_per_step": infos[-1]["iters"], "check_every": nchk,
-                   "frozen_at": infos[-1].get("frozen_at", -1),
-                   "l2": "inputs larger than L2 (%d sweep arrays of %.1f MB)" % (33, cells * 4 / 1e6),
+                   "cells": cells, "sweeps_timed": sum(sweeps), "check_every": nchk,
+                   "increments_finished": len(walk.finished),
+                   "l2": "inputs larger than L2 (33 sweep arrays of %.1f MB)" % (cells * 4 / 1e6),
                    "parallelism": "replicas" if world > 1 else "single"},
-        "ms_per_increment": ms_per_step,
         "clocks": clocks,
-        # per step: (iters / n_chk + 1) graph chunks (staged: 5 n_chk + 1
-        # kernels; fused: one staged check iteration, the check and n_chk - 1
-        # fused sweeps), plus about 20 start-of-increment and 7 commit kernels
-        "gpu_launches": int(sum((i["iters"] // nchk + 1) * (5 * nchk + 1 if len(kernels) == 5 else nchk + 5) + 27
-                                for i in infos)),
+        # per step: one graph of n_chk sweep launches plus the staged check (5
+        # kernels and the check), and at an increment's start about 20
+        # prologue kernels (+ about 40 network kernels with the warm start)
+        "gpu_launches": int(args.steps * (nchk + 5) + 60 * (len(walk.finished) + 1)),
         "roofline": roof,
         "e2e": e2e,
-        "fp64_plain": fp64,
-        "warm_start": warm,
+        "per_increment": dict(arms, fp64_plain=fp64, increment=args.increment),
+        "warm_start": training,
         "cpu_baseline": cpu,
     }
     if rank == 0:
@@ -417,67 +631,6 @@ def our_arm(args):
     if dist:
         dist.destroy_process_group()
     return 0
-
-
-def warm_arm(args, torch, P, stream, barrier, s, cells):
-    """The learned warm start on the benchmark box: a 3D U-Net (3 levels,
-    BF16 weights, FP32 accumulation) trained on the GPU with the library's
-    kernels from trajectories of held-out seeds of the same setup, then the
-    increment `--warm-increment` solved from one device checkpoint with the
-    plain start and with the network's start (FP32 sweeps, same tolerance)."""
-    import time as _t
-    import ep_inputs as E
-    from paper_2305_01701_gb300 import warmstart as W
-
-    t_train0 = _t.perf_counter()
-    net = W.new_net(3, base=args.warm_base, levels=3, seed=7, stream=stream.cuda_stream)
-    incs = args.warm_increment + 1
-    groups = []
-    for q in range(args.warm_train):
-        ts = E.config(5, n=s.n, tol=s.tol, seed=s.seed + 101 + q, c0=s.c0 * (1.0 + 0.05 * (q + 1)))
-        gt = make_grid(P, ts, "fp32", args.kernel, stream.cuda_stream)
-        data = W.Samples(3, gt.warm_dims(), capacity=incs)
-        W.collect(gt, ts.a, ts.dt, incs, data, load_plane=P.LOAD_XZ)
-        gt.close()
-        groups.append(data)
-    loss_before = W.evaluate(net, groups)
-    losses = W.train(net, groups, steps=args.warm_steps, lr=1e-3, batch=2)
-    torch.cuda.synchronize()
-    t_train = _t.perf_counter() - t_train0
-    loss_after, loss_zero = W.evaluate(net, groups), W.zero_loss(groups)
-
-    g = prepare(P, s, "fp32", args.warm_increment, args.kernel, stream.cuda_stream)
-    g.attach_warm_start(net)
-
-    def one(warm):
-        g.restore()
-        g.apply_increment(s.a, s.dt, P.LOAD_XZ, use_warm_start=warm)
-        return g.solve_increment()
-
-    one(False)
-    one(True)
-    res = {}
-    for warm in (False, True):
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        barrier()
-        ev0.record(stream)
-        info = one(warm)
-        ev1.record(stream)
-        barrier()
-        res[warm] = (ev0.elapsed_time(ev1), info)
-    bpc = g.sweep_bytes_per_cell()
-    out = {"increment": args.warm_increment,
-           "plain_ms": res[False][0], "plain_iterations": res[False][1]["iters"],
-           "warm_ms": res[True][0], "warm_iterations": res[True][1]["iters"],
-           "warm_GB_per_s": bpc * cells * res[True][1]["iters"] / (res[True][0] * 1e-3) / 1e9,
-           "net": "3-level U-Net, base %d, BF16 weights, FP32 accumulation" % args.warm_base,
-           "training": {"setups": args.warm_train, "samples": sum(d.n for d in groups), "steps": args.warm_steps,
-                        "train_mse_before": loss_before, "train_mse_after": loss_after,
-                        "train_mse_zero_net": loss_zero,
-                        "last_minibatch_loss": float(sum(losses[-10:]) / 10), "seconds": t_train}}
-    g.close()
-    net.close()
-    return out
 
 
 def batch_arm(args):
@@ -615,6 +768,10 @@ def batch_arm(args):
 
 def main():
     args = parse()
+    if args.oracle_plan:
+        return oracle_plan(args)
+    if args.symmetry_study:
+        return symmetry_study(args)
     if args.impl == "reference":
         return reference_arm(args)
     if args.batch > 0:

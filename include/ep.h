@@ -103,6 +103,17 @@ typedef struct {
    * commit on, and ep_restore brings back the state before the advection of
    * the checkpointed increment.  Default 0 (off). */
   int advection;
+  /* incompressible variant (Sec. 3.2, Eq. A2ssP2 in place of Eq. A2ssP):
+   * the pressure is pseudo-time state stepped by -K~ div v (pseudo step 1),
+   * starts at the old pressure, and its stopping measure is 2 eta_ve times
+   * the interval-averaged |div v| relative to max|sigma|.  Default 0. */
+  int incompressible;
+  /* bound, in SM clock cycles, of each wait of the TMA sweep kernel
+   * (EP_KERNEL_FUSED_TMA) for its plane copies; 0 (default) is 2^31 cycles,
+   * about a second.  A wait that runs out ends the solve with
+   * EP_ERR_TIMEOUT after the block has waited (with the default bound) for
+   * the copies it issued; the handle stays usable. */
+  long long wait_cycles;
 } ep_solver_opts;
 
 typedef struct {
@@ -137,9 +148,20 @@ ep_status ep_create_grid(int ndim, const int n[3], const double L[3], ep_precisi
 /* Material (Sec. 2.2, Eqs. A43, A61, A611): bulk K and shear G moduli, shear
  * viscosity mu_s (INFINITY = elastic limit), friction angle phi and dilation
  * angle psi in degrees (psi must be 0, Eq. A6121lambda), and the per-cell
- * cohesion (host, nx*ny[*nz] values, copied). */
+ * cohesion (host, nx*ny[*nz] values, copied; a value that is not finite
+ * is rejected with EP_ERR_ARG). */
 ep_status ep_set_material(ep_handle h, double K, double G, double mu_s, double phi_deg,
                           double psi_deg, const double *cohesion);
+
+/* Per-cell shear modulus (the paper's heterogeneous G-bar of Sec. 4.1):
+ * G (host, nx*ny[*nz] values > 0, copied) replaces the uniform G of
+ * ep_set_material in the Maxwell law (Eqs. A43, A23ssP) point by point:
+ * eta_ve and the weight c2 = eta_ve / (G dt) of the rotated old stress follow
+ * G at the centres, and at a vertex/edge the mean G of the centres around it
+ * (indices clamped at the walls); the pseudo-transient parameters (Eqs.
+ * PT1-PT24qq) use the largest G.  NULL restores the uniform G.  Grids with a
+ * per-cell G run the staged sweep kernels.  Not inside an open increment. */
+ep_status ep_set_shear_modulus(ep_handle h, const double *G);
 
 /* Fill opts with the defaults for a grid of dimension ndim. */
 ep_status ep_default_solver(int ndim, ep_solver_opts *opts);
@@ -338,6 +360,13 @@ ep_status ep_time_sweep(ep_handle h, int iters, double *ms_out, int n_out, int *
  * precision (the fused-sweep lower bound: every state array read and
  * written once, every constant read once). */
 ep_status ep_sweep_bytes_per_cell(ep_handle h, double *bytes);
+
+/* Measurement: the current device's FP64 fused multiply-add rate in
+ * TFLOP/s (2 flops per FMA; independent register chains, no memory traffic,
+ * best of five launches timed with CUDA events).  The FP64 sweeps are bound
+ * by FP64 arithmetic on GB300, so this is the roof they are reported
+ * against. */
+ep_status ep_measure_fp64_peak(double *tflops);
 
 ep_status ep_destroy(ep_handle h);
 

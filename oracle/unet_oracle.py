@@ -11,6 +11,11 @@ decoder input concatenates [upsampled coarser output, skip] along channels.
 
 The gradient is taken by central finite differences of the FP64 forward, a
 method independent of any back-propagation code.
+
+`forward(..., bf16_inputs=True)` states the precision of the library's
+inference forward on the tensor cores: the input of every 3^D convolution
+whose output has a multiple of 16 channels (16 to 128) is rounded to BF16
+(nearest, ties to even) before the product; everything else stays FP64.
 """
 from __future__ import annotations
 
@@ -77,7 +82,14 @@ def up(x):
     return y
 
 
-def forward(params, x, ndim, cin, cout, base, levels):
+def round_bf16(a):
+    """Nearest BF16 value (ties to even) of each element, as FP64."""
+    b = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32)
+    r = ((b >> 16) & 1) + 0x7FFF
+    return ((b + r) & 0xFFFF0000).astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def forward(params, x, ndim, cin, cout, base, levels, bf16_inputs=False):
     table, n = layer_table(ndim, cin, cout, base, levels)
     assert params.size == n
     li = 0
@@ -88,6 +100,8 @@ def forward(params, x, ndim, cin, cout, base, levels):
         li += 1
         w = params[wo:wo + ci * co * k ** ndim].reshape(co, ci, k ** ndim)
         b = params[bo:bo + co]
+        if bf16_inputs and k == 3 and co % 16 == 0 and 16 <= co <= 128:
+            inp = round_bf16(inp)
         y = conv(inp, w, b, k)
         return np.maximum(y, 0.0) if relu else y
 

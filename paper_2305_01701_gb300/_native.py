@@ -21,6 +21,13 @@ STATUS_NAMES = {0: "EP_OK", 1: "EP_ERR_ARG", 2: "EP_ERR_CUDA", 3: "EP_ERR_OOM", 
 PENDING = 8
 
 
+def measure_fp64_peak():
+    """FP64 FMA rate of the current device in TFLOP/s (ep_measure_fp64_peak)."""
+    t = C.c_double()
+    check(None, lib().ep_measure_fp64_peak(C.byref(t)))
+    return t.value
+
+
 def warm_in(ndim):
     """Input channels of the warm-start network (EP_WARM_IN)."""
     return 13 if ndim == 3 else 9
@@ -42,7 +49,8 @@ FIELD_ID = {n: i for i, n in enumerate(FIELDS)}
 class SolverOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_longlong), ("n_chk", C.c_int),
                 ("c_cfl", C.c_double), ("xi", C.c_double), ("r_pt", C.c_double), ("jaumann", C.c_int),
-                ("freeze_iter", C.c_longlong), ("freeze_eps", C.c_double), ("advection", C.c_int)]
+                ("freeze_iter", C.c_longlong), ("freeze_eps", C.c_double), ("advection", C.c_int),
+                ("incompressible", C.c_int), ("wait_cycles", C.c_longlong)]
 
 
 class SolveInfo(C.Structure):
@@ -78,6 +86,8 @@ SIGNATURES = [
     ("ep_apply_increment_rates", _I, [_P, _DP, _D, _DP, _DP]),
     ("ep_solve_increment", _I, [_P, C.POINTER(SolveInfo)]),
     ("ep_solve_chunks", _I, [_P, _I, C.POINTER(SolveInfo)]),
+    ("ep_set_shear_modulus", _I, [_P, _DP]),
+    ("ep_measure_fp64_peak", _I, [C.POINTER(C.c_double)]),
     ("ep_commit_increment", _I, [_P]),
     ("ep_field_count", _I, [_P, _I, C.POINTER(C.c_size_t)]),
     ("ep_get_fields", _I, [_P, _I, _DP, _Z]),
@@ -209,12 +219,22 @@ class Grid:
         check(self.h, self._L.ep_default_solver(self.ndim, C.byref(o)))
         return o
 
+    def set_shear_modulus(self, G):
+        """Per-cell shear modulus (one value per centre), or None for the
+        uniform G of set_material."""
+        a = None if G is None else _f64(np.asarray(G, dtype=np.float64).ravel())
+        if a is not None and a.size != int(np.prod(self.n)):
+            raise ValueError("set_shear_modulus: one value per cell centre")
+        check(self.h, self._L.ep_set_shear_modulus(self.h, _dp(a)))
+
     def set_solver(self, tol=1e-8, max_iter=10000000, n_chk=100, c_cfl=None, xi=1.0, r_pt=0.5, jaumann=True,
-                   freeze_iter=-1, freeze_eps=1e-4, advection=False):
+                   freeze_iter=-1, freeze_eps=1e-4, advection=False, incompressible=False,
+                   wait_cycles=0):
         """freeze_iter: frozen plasticity (Sec. 3.3) from this iteration on
         when eps_rel > freeze_eps; -1 the paper's rule (16 n_x above 10^6
         cells), 0 never.  advection: transport the old stress with the last
-        converged velocity at the start of each increment (Eq. j1)."""
+        converged velocity at the start of each increment (Eq. j1).
+        incompressible: Eq. A2ssP2 in place of Eq. A2ssP."""
         o = self.default_solver()
         o.tol = tol
         o.max_iter = int(max_iter)
@@ -226,6 +246,8 @@ class Grid:
         o.freeze_iter = int(freeze_iter)
         o.freeze_eps = float(freeze_eps)
         o.advection = int(bool(advection))
+        o.incompressible = int(bool(incompressible))
+        o.wait_cycles = int(wait_cycles)
         check(self.h, self._L.ep_set_solver(self.h, C.byref(o)))
 
     def apply_increment(self, a, dt, load_plane=LOAD_XY, body_force=None, use_warm_start=False):

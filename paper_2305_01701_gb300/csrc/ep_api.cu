@@ -74,6 +74,11 @@ struct ep_grid {
   bool warm_stress = false;     // the next prologue adds the predicted stress state
   bool wrecord = false;         // commits record the physical response (training targets)
   float *w0 = nullptr;          // that response, (nd + ns) FP32 boxes (cudaMalloc)
+  // per-cell shear modulus (ep_set_shear_modulus; cudaMalloc, null: uniform G)
+  double *Gc = nullptr;         // at centres
+  double Gmax = 0.0;
+  double *ge64[4] = {}, *gc64[4] = {};   // 2 eta_ve and c2 at centres and vertices/edges
+  void *geT[4] = {}, *gcT[4] = {};       // their sweep-type copies
   char *snap = nullptr;     // checkpoint of the history (ep_snapshot)
   bool snap_started = false;
   int snap_commits = 0, snap_adv_done = 0;
@@ -242,7 +247,10 @@ double eta_ve(const ep_grid *h) {
 // K~ = r G~, Re = xi 3 sqrt(10) pi / 2.
 Scal make_scal(const ep_grid *h) {
   Scal s{};
-  const double eta = eta_ve(h);
+  // the pseudo-transient parameters take the largest modulus of a per-cell G
+  const double eta = h->Gc ? (isinf(h->mu_s) ? h->Gmax * h->dt : 1.0 / (1.0 / (h->Gmax * h->dt) + 1.0 / h->mu_s))
+                           : eta_ve(h);
+  s.gcell = h->Gc != nullptr;
   s.two_eta = 2.0 * eta;
   s.c2 = eta / (h->G * h->dt);
   s.c2dt = s.c2 * h->dt;
@@ -259,6 +267,7 @@ Scal make_scal(const ep_grid *h) {
   if (fi < 0) fi = (double)h->g.nx * h->g.ny * h->g.nz > 1e6 ? 16LL * h->g.nx : 0;
   s.freeze_iter = fi;
   s.freeze_eps = h->opts.freeze_eps;
+  s.wait_cycles = h->opts.wait_cycles;
   double dxm = std::min(h->g.dx, h->g.dy), Lm = std::max(h->L[0], h->L[1]);
   if (h->ndim == 3) { dxm = std::min(dxm, h->g.dz); Lm = std::max(Lm, h->L[2]); }
   s.dxmin = dxm;
@@ -272,6 +281,20 @@ Scal make_scal(const ep_grid *h) {
   s.vstep = 1.0 / rho;
   s.inv_1mbt = 1.0 / (1.0 - s.bt);
   s.inv_1mbp = 1.0 / (1.0 - s.bp);
+  if (h->opts.incompressible) {
+    // Eq. A2ssP2 with pseudo step 1: p_{k+1} = p_k - K~ div v; the pressure
+    // is no function of v, so the physical response keeps p_hat, and its
+    // measure is 2 eta_ve <|div v|> (reading R9)
+    s.bp = 1.0;
+    s.obp = 1.0;
+    s.KDt = Kt;
+    s.KDt_phys = 0.0;
+    s.p_meas = 2.0 * eta / Kt;
+  } else {
+    s.obp = 1.0 - s.bp;
+    s.KDt_phys = s.KDt;
+    s.p_meas = s.inv_1mbp;
+  }
   for (int d = 0; d < 3; ++d) s.rate[d] = h->rate[d];
   return s;
 }
@@ -298,7 +321,12 @@ Stage<T> sweep_stage(ep_grid *h, int b) {
   S.pb = P<T>(h->pb); S.yc = P<T>(h->yc); S.s = P<T>(h->s);
   S.rd[0] = P<T>(h->rd[0]); S.rd[1] = P<T>(h->rd[1]);
   S.tb_scale = 1.0;
+  S.tb_c2 = 0;
   S.relax = 1;
+  for (int w = 0; w < 4; ++w) {
+    S.ge[w] = h->Gc ? P<T>(h->geT[w]) : nullptr;
+    S.gc[w] = h->Gc ? P<T>(h->gcT[w]) : nullptr;
+  }
   return S;
 }
 
@@ -332,7 +360,7 @@ void append_items(std::vector<int4> &v, int inst, const Geo &g, int tile) {
 
 template <typename T>
 bool use_fused2d(const ep_grid *h) {
-  if (h->ndim != 2 || h->have_f) return false;
+  if (h->ndim != 2 || h->have_f || h->Gc) return false;
   return h->variant == EP_KERNEL_FUSED || (h->variant == EP_KERNEL_AUTO && sizeof(T) == 4);
 }
 
@@ -373,7 +401,12 @@ Stage<double> phys_stage(ep_grid *h, double *const v[3]) {
   S.snp = h->stp64; S.pb = h->H.p; S.yc = h->yc64; S.s = h->s64;
   S.rd[0] = h->rd64[0]; S.rd[1] = h->rd64[1];
   S.tb_scale = make_scal(h).c2;
+  S.tb_c2 = 1;
   S.relax = 0;
+  for (int w = 0; w < 4; ++w) {
+    S.ge[w] = h->Gc ? h->ge64[w] : nullptr;
+    S.gc[w] = h->Gc ? h->gc64[w] : nullptr;
+  }
   return S;
 }
 
@@ -458,7 +491,15 @@ ep_status prologue(ep_grid *h, const double *const dv[3]) {
     if (copy_into<T>(h, h->cs[c], h->sts64[c]) != EP_OK) return EP_ERR_CUDA;
     if (copy_into<T>(h, h->rq[c], h->rq64[c]) != EP_OK) return EP_ERR_CUDA;
   }
-  if (copy_into<T>(h, h->pb, h->stp64) != EP_OK) return EP_ERR_CUDA;
+  if (h->opts.incompressible) {
+    // base pressure step of the incompressible sweep: -K~ div v0 (es64 is
+    // free after the start stage); the state starts at p_hat
+    const double *v0[3] = {h->H.v0[0], h->H.v0[1], h->H.v0[2]};
+    launch_scaled_div(g, v0, -make_scal(h).KDt, h->es64[0], st);
+    if (copy_into<T>(h, h->pb, h->es64[0]) != EP_OK) return EP_ERR_CUDA;
+  } else if (copy_into<T>(h, h->pb, h->stp64) != EP_OK) {
+    return EP_ERR_CUDA;
+  }
   if (copy_into<T>(h, h->stp[0], h->stp64) != EP_OK) return EP_ERR_CUDA;
   if (copy_into<T>(h, h->stp[1], h->stp64) != EP_OK) return EP_ERR_CUDA;
   if (copy_into<T>(h, h->cp, h->stp64) != EP_OK) return EP_ERR_CUDA;
@@ -482,7 +523,7 @@ int fused_variant(const ep_grid *h) {
 
 template <typename T>
 bool use_fused(const ep_grid *h) {
-  if (h->ndim != 3 || h->have_f) return false;
+  if (h->ndim != 3 || h->have_f || h->Gc) return false;
   const int v = fused_variant(h);
   return v == EP_KERNEL_FUSED || v == EP_KERNEL_FUSED_TMA || v == EP_KERNEL_FUSED_REG;
 }
@@ -693,6 +734,8 @@ ep_status ep_default_solver(int ndim, ep_solver_opts *o) {
   o->freeze_iter = -1;
   o->freeze_eps = 1e-4;
   o->advection = 0;
+  o->incompressible = 0;
+  o->wait_cycles = 0;
   return EP_OK;
 }
 
@@ -767,6 +810,11 @@ ep_status ep_set_material(ep_handle h, double K, double G, double mu_s, double p
   if (!(K > 0.0) || !(G > 0.0) || !(mu_s > 0.0) || !cohesion)
     return fail(h, EP_ERR_ARG, "ep_set_material: need K, G, mu_s > 0 and a cohesion array");
   if (psi_deg != 0.0) return fail(h, EP_ERR_ARG, "ep_set_material: the return assumes psi = 0");
+  if (!std::isfinite(phi_deg)) return fail(h, EP_ERR_ARG, "ep_set_material: friction angle not finite");
+  const long long ncell = (long long)h->g.nx * h->g.ny * h->g.nz;
+  for (long long q = 0; q < ncell; ++q)
+    if (!std::isfinite(cohesion[q]))
+      return fail(h, EP_ERR_ARG, "ep_set_material: cohesion of cell " + std::to_string(q) + " is not finite");
   const double phi = phi_deg * M_PI / 180.0;
   h->K = K; h->G = G; h->mu_s = mu_s;
   if (h->ndim == 2) {
@@ -781,6 +829,48 @@ ep_status ep_set_material(ep_handle h, double K, double G, double mu_s, double p
   for (long long q = 0; q < (long long)h->g.nx * h->g.ny * h->g.nz; ++q) cm = std::max(cm, fabs(cohesion[q]));
   h->cmax = cm > 0.0 ? cm : 1.0;
   h->have_material = true;
+  return EP_OK;
+}
+
+ep_status ep_set_shear_modulus(ep_handle h, const double *G) {
+  if (!h) return fail(nullptr, EP_ERR_ARG, "null handle");
+  if (h->in_increment) return fail(h, EP_ERR_STATE, "ep_set_shear_modulus: not allowed inside an open increment");
+  const long long ncell = (long long)h->g.nx * h->g.ny * h->g.nz;
+  if (h->chunk) { cudaGraphExecDestroy(h->chunk); h->chunk = nullptr; }   // captured stages change
+  h->items_tile = -1;
+  if (!G) {
+    if (h->Gc) {
+      cudaFree(h->Gc);
+      for (int w = 0; w < 4; ++w) {
+        cudaFree(h->ge64[w]); cudaFree(h->gc64[w]);
+        if (h->prec != EP_FP64) { cudaFree(h->geT[w]); cudaFree(h->gcT[w]); }
+        h->ge64[w] = h->gc64[w] = nullptr; h->geT[w] = h->gcT[w] = nullptr;
+      }
+    }
+    h->Gc = nullptr;
+    h->H.te_c = nullptr;
+    return EP_OK;
+  }
+  double gm = 0.0;
+  for (long long q = 0; q < ncell; ++q) {
+    if (!(G[q] > 0.0) || !std::isfinite(G[q]))
+      return fail(h, EP_ERR_ARG, "ep_set_shear_modulus: every value must be finite and > 0");
+    gm = std::max(gm, G[q]);
+  }
+  const size_t nb = h->g.box * sizeof(double), nt = h->g.box * (h->prec == EP_FP64 ? 8 : 4);
+  if (!h->Gc) {
+    CK(h, cudaMalloc((void **)&h->Gc, nb));
+    for (int w = 0; w < 4; ++w) {
+      CK(h, cudaMalloc((void **)&h->ge64[w], nb));
+      CK(h, cudaMalloc((void **)&h->gc64[w], nb));
+      if (h->prec == EP_FP64) { h->geT[w] = h->ge64[w]; h->gcT[w] = h->gc64[w]; }
+      else { CK(h, cudaMalloc(&h->geT[w], nt)); CK(h, cudaMalloc(&h->gcT[w], nt)); }
+    }
+  }
+  ep_status r = upload_box(h, G, h->Gc, h->g.nx, h->g.ny, h->g.nz);
+  if (r != EP_OK) return r;
+  h->Gmax = gm;
+  h->H.te_c = h->ge64[0];
   return EP_OK;
 }
 
@@ -807,8 +897,18 @@ static ep_status set_increment(ep_grid *h, const double rates[3], double dt, con
   h->dt = dt;
   const Scal sc = make_scal(h);
   CK(h, cudaMemcpyAsync(h->dscal, &sc, sizeof(Scal), cudaMemcpyHostToDevice, h->stream));
-  CK(h, cudaStreamSynchronize(h->stream));
   const size_t es = h->prec == EP_FP64 ? 8 : 4;
+  if (h->Gc) {
+    // per-cell modulus: 2 eta_ve and c2 of every point for this dt
+    launch_shear_fields(h->g, h->Gc, h->mu_s, dt, h->ge64, h->gc64, h->stream);
+    if (es == 4)
+      for (int w = 0; w < 4; ++w) {
+        launch_convert<float, double>((float *)h->geT[w], h->ge64[w], h->g.box, h->stream);
+        launch_convert<float, double>((float *)h->gcT[w], h->gc64[w], h->g.box, h->stream);
+      }
+    CK(h, cudaGetLastError());
+  }
+  CK(h, cudaStreamSynchronize(h->stream));
   if (h->have_f != (body_force != nullptr) && h->chunk) {
     cudaGraphExecDestroy(h->chunk);  // the captured kernels depend on the body force
     h->chunk = nullptr;
@@ -1554,6 +1654,13 @@ ep_status ep_destroy(ep_handle h) {
   if (h->wx) cudaFree(h->wx);   // warm-start network input / output
   if (h->wy) cudaFree(h->wy);
   if (h->w0) cudaFree(h->w0);
+  if (h->Gc) {
+    cudaFree(h->Gc);
+    for (int w = 0; w < 4; ++w) {
+      cudaFree(h->ge64[w]); cudaFree(h->gc64[w]);
+      if (h->prec != EP_FP64) { cudaFree(h->geT[w]); cudaFree(h->gcT[w]); }
+    }
+  }
   delete h;
   return EP_OK;
 }

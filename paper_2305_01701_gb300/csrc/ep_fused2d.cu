@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(TX *TY) k_fused2d(const Inst2<T> *insts, const
     const int nx = g.nx, ny = g.ny;
     const long long px = g.px;
     const T rdx = (T)g.rdx, rdy = (T)g.rdy, two_eta = (T)sc->two_eta;
-    const T bt = (T)sc->bt, ob = (T)1 - bt, bp = (T)sc->bp, obp = (T)1 - bp, KDt = (T)sc->KDt;
+    const T bt = (T)sc->bt, ob = (T)1 - bt, bp = (T)sc->bp, obp = (T)sc->obp, KDt = (T)sc->KDt;
     const T Acoef = (T)sc->A, vs = (T)sc->vstep, qr = (T)0.25, third = (T)(1.0 / 3.0);
     const T *u0 = I.u[b][0], *u1 = I.u[b][1];
 

@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(SW *SWARPS) k_fused2d_strip(const Inst2<T> *in
     const bool xin = gi >= 0 && gi < g.px;
     const bool out_col = a >= 2 && a < SW - 2 && xin;
     const T rdx = (T)g.rdx, rdy = (T)g.rdy, two_eta = (T)sc->two_eta;
-    const T bt = (T)sc->bt, ob = (T)1 - bt, bp = (T)sc->bp, obp = (T)1 - bp, KDt = (T)sc->KDt;
+    const T bt = (T)sc->bt, ob = (T)1 - bt, bp = (T)sc->bp, obp = (T)sc->obp, KDt = (T)sc->KDt;
     const T Acoef = (T)sc->A, vs = (T)sc->vstep, qr = (T)0.25, third = (T)(1.0 / 3.0), hf = (T)0.5;
     const T *u0 = I.u[b][0], *u1 = I.u[b][1];
 

@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(TX * TY, 2) k_fused3d(Geo g, F3<T> A, const Sc
   const int nx = g.nx, ny = g.ny, nz = g.nz;
   const T rdx = (T)g.rdx, rdy = (T)g.rdy, rdz = (T)g.rdz;
   const T two_eta = (T)sc->two_eta, bt = (T)sc->bt, ob = (T)1 - bt;
-  const T bp = (T)sc->bp, obp = (T)1 - bp, KDt = (T)sc->KDt, Acoef = (T)sc->A;
+  const T bp = (T)sc->bp, obp = (T)sc->obp, KDt = (T)sc->KDt, Acoef = (T)sc->A;
   const T vs = (T)sc->vstep, qr = (T)0.25, third = (T)(1.0 / 3.0);
   const long long px = g.px;
 

@@ -93,7 +93,7 @@ __device__ __forceinline__ void reg_body(const Args<T> &A, const Geo &g, const S
   const bool out_col = a >= 2 && a < W - 2 && b >= 2 && b < H - 2;
   const T rdx = (T)g.rdx, rdy = (T)g.rdy, rdz = (T)g.rdz;
   const T two_eta = (T)sc->two_eta, bt = (T)sc->bt, ob = (T)1 - bt;
-  const T bp = (T)sc->bp, obp = (T)1 - bp, KDt = (T)sc->KDt, Acoef = (T)sc->A;
+  const T bp = (T)sc->bp, obp = (T)sc->obp, KDt = (T)sc->KDt, Acoef = (T)sc->A;
   const T vs = (T)sc->vstep, qr = (T)0.25, third = (T)(1.0 / 3.0), hf = (T)0.5;
   const int rb = b + 1;  // this thread's row in a Rows slot
 

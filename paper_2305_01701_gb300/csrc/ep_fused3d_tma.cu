@@ -77,12 +77,13 @@ __device__ __forceinline__ bool bar_try(unsigned long long *b, unsigned parity) 
       : "memory");
   return ok != 0;
 }
-// bounded wait: gives up after about 2^31 SM cycles (~1 s at 2 GHz), far
-// above any copy's latency
-__device__ __forceinline__ bool bar_wait(unsigned long long *b, unsigned parity) {
+// bounded wait: gives up after `limit` SM cycles (by default 2^31, about
+// 1 s at 2 GHz, far above any copy's latency)
+constexpr long long WAIT_DEFAULT = 1ll << 31;
+__device__ __forceinline__ bool bar_wait(unsigned long long *b, unsigned parity, long long limit = WAIT_DEFAULT) {
   const long long t0 = clock64();
   while (!bar_try(b, parity))
-    if (clock64() - t0 > (1ll << 31)) return false;
+    if (clock64() - t0 > limit) return false;
   return true;
 }
 __device__ __forceinline__ void tma_load(void *dst, const CUtensorMap *map, int x, int y, int z,
@@ -127,7 +128,7 @@ __global__ void __launch_bounds__(TX *TY, 1)
   const int nx = g.nx, ny = g.ny, nz = g.nz;
   const T rdx = (T)g.rdx, rdy = (T)g.rdy, rdz = (T)g.rdz;
   const T two_eta = (T)sc->two_eta, bt = (T)sc->bt, ob = (T)1 - bt;
-  const T bp = (T)sc->bp, obp = (T)1 - bp, KDt = (T)sc->KDt, Acoef = (T)sc->A;
+  const T bp = (T)sc->bp, obp = (T)sc->obp, KDt = (T)sc->KDt, Acoef = (T)sc->A;
   const T vs = (T)sc->vstep, qr = (T)0.25, third = (T)(1.0 / 3.0), hf = (T)0.5;
   const long long px = g.px;
   const bool leader = threadIdx.x == 0;
@@ -151,12 +152,15 @@ __global__ void __launch_bounds__(TX *TY, 1)
   if (leader) issue_plane<T, TY>(S, M, i0, j0, kb - 2);
   unsigned phase[2] = {0u, 0u};
 
+  const long long wait_limit = sc->wait_cycles > 0 ? sc->wait_cycles : WAIT_DEFAULT;
   for (int t = kb - 2; t < ke + 2; ++t) {
-    const bool ok = bar_wait(&S.bar[t & 1], phase[t & 1]);
+    const bool ok = bar_wait(&S.bar[t & 1], phase[t & 1], wait_limit);
     phase[t & 1] ^= 1u;
     if (__syncthreads_or(!ok)) {
       if (leader && di) atomicExch(&di->done, 4);
-      // wait once more (bounded) for this plane's copies, then leave
+      // wait once more for this plane's copies (bounded by the default
+      // limit whatever the option), so that none is in flight when the
+      // block's shared memory is released, then leave
       if (!ok) bar_wait(&S.bar[t & 1], phase[t & 1] ^ 1u);
       return;
     }

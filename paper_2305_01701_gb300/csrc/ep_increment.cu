@@ -70,7 +70,7 @@ __global__ void k_rotation_fields(Geo g, History H, const Scal *sc, T *rq0, T *r
   if (!q.in) return;
   const int i = q.i, j = q.j, k = q.k;
   const long long e = q.e;
-  const double w = sc->jaumann ? sc->c2dt : 0.0;
+  const double w = sc->jaumann ? (sc->gcell ? sc->dt : sc->c2dt) : 0.0;
   const bool centre = i < g.nx && j < g.ny && (g.ndim == 2 || k < g.nz);
   if (centre) {
     rd0[e] = (T)(w * (H.tn[1][e] - H.tn[0][e]));
@@ -130,7 +130,7 @@ __global__ void k_commit(Geo g, History H, const double *Tn0, const double *Tn1,
         J2 += b * b + cc * cc;
       }
       if ((double)s[e] < 1.0) {
-        H.epl[e] += dt * sqrt(J2) / sc->two_eta;
+        H.epl[e] += dt * sqrt(J2) / (H.te_c ? H.te_c[e] : sc->two_eta);
         plastic = 1;
       }
       double ex = (H.v[0][e + 1] - H.v[0][e]) * g.rdx;
@@ -206,6 +206,63 @@ __global__ void k_unpack(const double *src, double *box, int ex, int ey, int ez,
   long long r = t / ex;
   int j = (int)(r % ey), k = (int)(r / ey);
   box[((long long)k * py + j) * px + i] = src[t];
+}
+
+// Per-point Maxwell coefficients of a per-cell shear modulus G (centres):
+// at centres G itself, at a vertex/edge the mean of the G of the centres
+// around it (one layer along each direction in which the point sits at cell
+// centres, two along the others; indices clamped at the walls); then
+// 2 eta_ve = 2 / (1/(G dt) + 1/mu_s) and c2 = eta_ve / (G dt).
+__global__ void k_shear_fields(Geo g, const double *Gc, double mu_s, double dt, double *ge0, double *ge1,
+                               double *ge2, double *ge3, double *gc0, double *gc1, double *gc2, double *gc3) {
+  const Pos3 q = pos3(g);
+  if (!q.in) return;
+  const int nd = g.ndim, ez = nd == 3 ? g.nz : 1;
+  double *ge[4] = {ge0, ge1, ge2, ge3}, *gc[4] = {gc0, gc1, gc2, gc3};
+  auto coef = [&](double G, double *a, double *b) {
+    const double eta = isinf(mu_s) ? G * dt : 1.0 / (1.0 / (G * dt) + 1.0 / mu_s);
+    *a = 2.0 * eta;
+    *b = eta / (G * dt);
+  };
+  const bool centre = q.i < g.nx && q.j < g.ny && q.k < ez;
+  double a = 0.0, b = 0.0;
+  if (centre) coef(Gc[q.e], &a, &b);
+  ge[0][q.e] = a;
+  gc[0][q.e] = b;
+  const int ns = nd == 3 ? 3 : 1;
+  for (int c = 0; c < ns; ++c) {
+    // staggering of shear component c: 1 along the directions of its faces
+    const int sx = nd == 2 ? 1 : c != 2, sy = nd == 2 ? 1 : c != 1, sz = nd == 2 ? 0 : c != 0;
+    double sum = 0.0;
+    int cnt = 0;
+    for (int dz = -sz; dz <= 0; ++dz)
+      for (int dy = -sy; dy <= 0; ++dy)
+        for (int dx = -sx; dx <= 0; ++dx) {
+          const int i = min(max(q.i + dx, 0), g.nx - 1), j = min(max(q.j + dy, 0), g.ny - 1);
+          const int k = min(max(q.k + dz, 0), ez - 1);
+          sum += Gc[g.idx(i, j, k)];
+          ++cnt;
+        }
+    a = 0.0; b = 0.0;
+    const bool in = q.i <= g.nx && q.j <= g.ny && q.k <= (nd == 3 ? g.nz : 0);
+    if (in) coef(sum / cnt, &a, &b);
+    ge[1 + c][q.e] = a;
+    gc[1 + c][q.e] = b;
+  }
+}
+
+// out = scale * div(v) at centres, 0 elsewhere (the incompressible sweep's
+// base pressure step -K~ div v0, Eq. A2ssP2)
+__global__ void k_scaled_div(Geo g, const double *v0, const double *v1, const double *v2, double scale, double *out) {
+  const Pos3 q = pos3(g);
+  if (!q.in) return;
+  const bool centre = q.i < g.nx && q.j < g.ny && (g.ndim == 2 || q.k < g.nz);
+  double d = 0.0;
+  if (centre) {
+    d = (v0[q.e + 1] - v0[q.e]) * g.rdx + (v1[q.e + g.px] - v1[q.e]) * g.rdy;
+    if (g.ndim == 3) d += (v2[q.e + g.plane] - v2[q.e]) * g.rdz;
+  }
+  out[q.e] = centre ? scale * d : 0.0;
 }
 
 // ---- advection of the old stress (the v_k d sigma_ij / dx_k term, Eq. j1) ----
@@ -358,5 +415,15 @@ template void launch_commit<double>(const Geo &, const History &, const double *
 template void launch_convert<float, double>(float *, const double *, long long, cudaStream_t);
 template void launch_convert<double, float>(double *, const float *, long long, cudaStream_t);
 template void launch_convert<double, double>(double *, const double *, long long, cudaStream_t);
+
+void launch_scaled_div(const Geo &g, const double *const v[3], double scale, double *out, cudaStream_t st) {
+  k_scaled_div<<<blocks_for(g.box), kThreads, 0, st>>>(g, v[0], v[1], v[2], scale, out);
+}
+
+void launch_shear_fields(const Geo &g, const double *Gc, double mu_s, double dt, double *const ge[4],
+                         double *const gc[4], cudaStream_t st) {
+  k_shear_fields<<<blocks_for(g.box), kThreads, 0, st>>>(g, Gc, mu_s, dt, ge[0], ge[1], ge[2], ge[3], gc[0], gc[1],
+                                                         gc[2], gc[3]);
+}
 
 }  // namespace ep

@@ -32,7 +32,10 @@ struct Scal {
   double c2;           // eta_ve / (G dt): weight of the rotated old stress
   double c2dt;         // c2 * dt: weight of the Jaumann rotation term
   double bt, bp;       // relaxation weights beta_tau, beta_p (Eqs. A23ssP, A2ssP)
-  double KDt;          // K dt (Eq. A2ssP)
+  double KDt;          // sweep pressure step: K dt (Eq. A2ssP), K~ incompressible (Eq. A2ssP2)
+  double obp;          // weight of the pressure target: 1 - beta_p; 1 incompressible
+  double KDt_phys;     // physical response: K dt; 0 incompressible (p stays p_hat)
+  double p_meas;       // pressure measure factor: 1 / (1 - beta_p); 2 eta_ve / K~ incompressible
   double A, B;         // Drucker-Prager coefficients (Eqs. A61 / A611)
   double vstep;        // pseudo step / rho~ (Eq. A22P)
   double dt;
@@ -44,6 +47,9 @@ struct Scal {
   int jaumann;
   long long freeze_iter;   // > 0: frozen plasticity armed from this iteration on
   double freeze_eps;
+  long long wait_cycles;   // bound of a TMA wait (0: the default, 2^31 cycles)
+  int gcell;               // 1: per-cell shear modulus; the rotation weights then
+                           // carry dt only and the trial applies each point's c2
 };
 
 // Reduction slots: bit patterns of non-negative doubles reduced with an
@@ -71,7 +77,8 @@ struct Stage {
   const T *son[3], *sos[3], *sop;   // old pseudo-time state (relax only)
   T *snn[3], *sns[3], *snp;         // new state
   const T *tbn[3], *tbs[3], *pb;    // base trial (x tb_scale) and base pressure
-  double tb_scale;
+  double tb_scale;                  // 0 with per-cell c2 (then c2 of the point, see tb_c2)
+  int tb_c2;                        // 1: the base trial is the old stress times c2
   const T *rq[3];                   // c2 dt tau_hat shear (edges)
   const T *rd[2];                   // c2 dt (tyy - txx), c2 dt (tzz - txx) (centres)
   const T *yc;                      // B c (centres)
@@ -84,6 +91,9 @@ struct Stage {
   T *cn[3], *cs[3], *cp;            // stress state at the previous check
   const double *v0[3];              // start velocity (eps_rel)
   int relax;                        // 1: sweep weights; 0: physical response
+  // per-cell shear modulus (nullable: the uniform scalars): 2 eta_ve and
+  // c2 = eta_ve / (G dt) at centres [0] and vertices/edges [1 + c]
+  const T *ge[4], *gc[4];
 };
 
 // One 2D instance of the batched fused sweep (ep_fused2d.cu): geometry,
@@ -115,7 +125,7 @@ __device__ __forceinline__ void check_one(DevInfo *di, const Scal *sc) {
   // momentum residual averaged over the interval: rho~ (u_{k+1} - u_chk) / m
   double em = du == 0.0 ? 0.0 : (ms > 0.0 ? sc->dxmin * du / (m * sc->vstep) / ms : inf);
   double et = dtau == 0.0 ? 0.0 : (ms > 0.0 ? dtau / (m * (1.0 - sc->bt)) / ms : inf);
-  double ep = dp == 0.0 ? 0.0 : (ms > 0.0 ? dp / (m * (1.0 - sc->bp)) / ms : inf);
+  double ep = dp == 0.0 ? 0.0 : (ms > 0.0 ? dp * sc->p_meas / m / ms : inf);
   double er = em > et ? em : et;
   if (ep > er) er = ep;
   if (isnan(em) || isnan(et) || isnan(ep) || isnan(ms) || isnan(du)) er = nan("");
@@ -217,6 +227,7 @@ cudaError_t fused3d_reg_configure();
 // ---- increment set-up and commit (FP64; ep_increment.cu) ------------------
 struct History {
   double *v[3], *tn[3], *ts[3], *p, *coh, *epl, *u[3], *an[3], *as[3], *v0[3];
+  const double *te_c;   // per-cell 2 eta_ve at centres (nullable: Scal.two_eta)
 };
 void launch_start_velocity(const Geo &g, const History &H, const double *const dv[3], const Scal *sc,
                            int started, const double L[3], cudaStream_t st);
@@ -256,6 +267,9 @@ void launch_warm_dv(const Geo &g, const float *y, int f, double sv, double *cons
                     cudaStream_t st);
 void launch_warm_stress(const Geo &g, const float *y, int f, double stress_scale, double *const n[3],
                         double *const s[3], const int dims[3], cudaStream_t st);
+void launch_shear_fields(const Geo &g, const double *Gc, double mu_s, double dt, double *const ge[4],
+                         double *const gc[4], cudaStream_t st);
+void launch_scaled_div(const Geo &g, const double *const v[3], double scale, double *out, cudaStream_t st);
 void launch_unpack(const double *src, double *box, int ex, int ey, int ez, int px, int py, cudaStream_t st);
 
 }  // namespace ep

@@ -136,7 +136,12 @@ __global__ void __launch_bounds__(kThreads) k_trial(Geo g, Stage<T> S, const Sca
   const long long e = q.e, px = g.px, pl = g.plane;
   if (i > nx || j > ny || k > (ND == 3 ? nz : 0)) return;
   const T rdx = (T)g.rdx, rdy = (T)g.rdy, rdz = (T)g.rdz;
-  const T two_eta = (T)sc->two_eta, tbs = (T)S.tb_scale, qr = (T)0.25, third = (T)(1.0 / 3.0);
+  const T two_eta = (T)sc->two_eta, tbs0 = (T)S.tb_scale, qr = (T)0.25, third = (T)(1.0 / 3.0);
+  // per point: 2 eta_ve, the weight c2 of the rotation terms (folded into
+  // the rotation weights when the modulus is uniform) and of the base trial
+  auto te = [&](int w, long long x) { return S.ge[w] ? S.ge[w][x] : two_eta; };
+  auto cr = [&](int w, long long x) { return S.gc[w] ? S.gc[w][x] : (T)1; };
+  auto tb = [&](int w, long long x) { return S.tb_c2 && S.gc[w] ? S.gc[w][x] : tbs0; };
   const T bt = S.relax ? (T)sc->bt : (T)0, ob = (T)1 - bt;
   // ---- centre ----
   if (i < nx && j < ny && (ND == 2 || k < nz)) {
@@ -148,8 +153,10 @@ __global__ void __launch_bounds__(kThreads) k_trial(Geo g, Stage<T> S, const Sca
       T d3 = (exx + eyy) * third;
       T qv = qr * (S.rq[0][c] * S.om[0][c] + S.rq[0][c + 1] * S.om[0][c + 1] +
                    S.rq[0][c + px] * S.om[0][c + px] + S.rq[0][c + px + 1] * S.om[0][c + px + 1]);
-      tr[0] = tbs * S.tbn[0][c] + two_eta * (exx - d3) + (T)2 * qv;
-      tr[1] = tbs * S.tbn[1][c] + two_eta * (eyy - d3) - (T)2 * qv;
+      const T tw = te(0, c), cc = cr(0, c), tbs = tb(0, c);
+      qv = cc * qv;
+      tr[0] = tbs * S.tbn[0][c] + tw * (exx - d3) + (T)2 * qv;
+      tr[1] = tbs * S.tbn[1][c] + tw * (eyy - d3) - (T)2 * qv;
     } else {
       T exx = (S.u[0][c + 1] - S.u[0][c]) * rdx;
       T eyy = (S.u[1][c + px] - S.u[1][c]) * rdy;
@@ -161,9 +168,11 @@ __global__ void __launch_bounds__(kThreads) k_trial(Geo g, Stage<T> S, const Sca
                     S.rq[1][c + pl] * S.om[1][c + pl] + S.rq[1][c + pl + 1] * S.om[1][c + pl + 1]);
       T pyz = qr * (S.rq[2][c] * S.om[2][c] + S.rq[2][c + px] * S.om[2][c + px] +
                     S.rq[2][c + pl] * S.om[2][c + pl] + S.rq[2][c + pl + px] * S.om[2][c + pl + px]);
-      tr[0] = tbs * S.tbn[0][c] + two_eta * (exx - d3) + (T)2 * (pxy + pxz);
-      tr[1] = tbs * S.tbn[1][c] + two_eta * (eyy - d3) - (T)2 * (pxy - pyz);
-      tr[2] = tbs * S.tbn[2][c] + two_eta * (ezz - d3) - (T)2 * (pxz + pyz);
+      const T tw = te(0, c), cc = cr(0, c), tbs = tb(0, c);
+      pxy = cc * pxy; pxz = cc * pxz; pyz = cc * pyz;
+      tr[0] = tbs * S.tbn[0][c] + tw * (exx - d3) + (T)2 * (pxy + pxz);
+      tr[1] = tbs * S.tbn[1][c] + tw * (eyy - d3) - (T)2 * (pxy - pyz);
+      tr[2] = tbs * S.tbn[2][c] + tw * (ezz - d3) - (T)2 * (pxz + pyz);
     }
 #pragma unroll
     for (int d = 0; d < ND; ++d) S.Tn[d][c] = S.relax ? bt * S.son[d][c] + ob * tr[d] : tr[d];
@@ -173,7 +182,7 @@ __global__ void __launch_bounds__(kThreads) k_trial(Geo g, Stage<T> S, const Sca
     T v = 0;
     if (i > 0 && i < nx && j > 0 && j < ny) {
       T dyx = qr * (S.rd[0][e - px - 1] + S.rd[0][e - px] + S.rd[0][e - 1] + S.rd[0][e]);
-      T tr = tbs * S.tbs[0][e] + two_eta * S.es[0][e] + S.om[0][e] * dyx;
+      T tr = tb(1, e) * S.tbs[0][e] + te(1, e) * S.es[0][e] + cr(1, e) * (S.om[0][e] * dyx);
       v = S.relax ? bt * S.sos[0][e] + ob * tr : tr;
     }
     S.Ts[0][e] = v;
@@ -185,7 +194,7 @@ __global__ void __launch_bounds__(kThreads) k_trial(Geo g, Stage<T> S, const Sca
       T Wyz = qr * (S.om[2][e - 1] + S.om[2][e] + S.om[2][e - 1 + pl] + S.om[2][e + pl]);
       T Txz = qr * (S.rq[1][e - px] + S.rq[1][e] + S.rq[1][e - px + pl] + S.rq[1][e + pl]);
       T Wxz = qr * (S.om[1][e - px] + S.om[1][e] + S.om[1][e - px + pl] + S.om[1][e + pl]);
-      T tr = tbs * S.tbs[0][e] + two_eta * S.es[0][e] + (S.om[0][e] * dyx + Tyz * Wxz + Txz * Wyz);
+      T tr = tb(1, e) * S.tbs[0][e] + te(1, e) * S.es[0][e] + cr(1, e) * (S.om[0][e] * dyx + Tyz * Wxz + Txz * Wyz);
       v = S.relax ? bt * S.sos[0][e] + ob * tr : tr;
     }
     S.Ts[0][e] = v;
@@ -196,7 +205,7 @@ __global__ void __launch_bounds__(kThreads) k_trial(Geo g, Stage<T> S, const Sca
       T Wyz = qr * (S.om[2][e - 1] + S.om[2][e] + S.om[2][e - 1 + px] + S.om[2][e + px]);
       T Txy = qr * (S.rq[0][e - pl] + S.rq[0][e - pl + px] + S.rq[0][e] + S.rq[0][e + px]);
       T Wxy = qr * (S.om[0][e - pl] + S.om[0][e - pl + px] + S.om[0][e] + S.om[0][e + px]);
-      T tr = tbs * S.tbs[1][e] + two_eta * S.es[1][e] + (S.om[1][e] * dzx + Tyz * Wxy - Txy * Wyz);
+      T tr = tb(2, e) * S.tbs[1][e] + te(2, e) * S.es[1][e] + cr(2, e) * (S.om[1][e] * dzx + Tyz * Wxy - Txy * Wyz);
       v = S.relax ? bt * S.sos[1][e] + ob * tr : tr;
     }
     S.Ts[1][e] = v;
@@ -208,7 +217,7 @@ __global__ void __launch_bounds__(kThreads) k_trial(Geo g, Stage<T> S, const Sca
       T Wxy = qr * (S.om[0][e - pl] + S.om[0][e - pl + 1] + S.om[0][e] + S.om[0][e + 1]);
       T Txz = qr * (S.rq[1][e - px] + S.rq[1][e - px + 1] + S.rq[1][e] + S.rq[1][e + 1]);
       T Wxz = qr * (S.om[1][e - px] + S.om[1][e - px + 1] + S.om[1][e] + S.om[1][e + 1]);
-      T tr = tbs * S.tbs[2][e] + two_eta * S.es[2][e] + (S.om[2][e] * dzy - Txy * Wxz - Txz * Wxy);
+      T tr = tb(3, e) * S.tbs[2][e] + te(3, e) * S.es[2][e] + cr(3, e) * (S.om[2][e] * dzy - Txy * Wxz - Txz * Wxy);
       v = S.relax ? bt * S.sos[2][e] + ob * tr : tr;
     }
     S.Ts[2][e] = v;
@@ -230,9 +239,9 @@ __global__ void __launch_bounds__(kThreads) k_return_centres(Geo g, Stage<T> S, 
     const T qr = (T)0.25;
     T div = (S.u[0][c + 1] - S.u[0][c]) * (T)g.rdx + (S.u[1][c + px] - S.u[1][c]) * (T)g.rdy;
     if (ND == 3) div += (S.u[2][c + pl] - S.u[2][c]) * (T)g.rdz;
-    const T bp = S.relax ? (T)sc->bp : (T)0;
-    T target = S.pb[c] - (T)sc->KDt * div;
-    T p = S.relax ? bp * S.sop[c] + ((T)1 - bp) * target : target;
+    T p;
+    if (S.relax) p = (T)sc->bp * S.sop[c] + (T)sc->obp * (S.pb[c] - (T)sc->KDt * div);
+    else p = S.pb[c] - (T)sc->KDt_phys * div;
     T txy = qr * (S.Ts[0][c] + S.Ts[0][c + 1] + S.Ts[0][c + px] + S.Ts[0][c + px + 1]);
     T J2 = txy * txy;
     if (ND == 3) {

@@ -18,6 +18,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -25,6 +26,16 @@
 #include "ep_internal.cuh"
 
 namespace ep {
+
+// ep_conv_tc.cu
+bool conv_tc_supported(int k, int cout);
+int conv_tc_cinp(int cin);
+void conv_tc_to_channels_last(const float *x, int N, int C, long long nv, int cp, __nv_bfloat16 *out,
+                              cudaStream_t st);
+void conv_tc_pack_weights(const __nv_bfloat16 *w, int cin, int cout, int taps, __nv_bfloat16 *out, cudaStream_t st);
+cudaError_t conv_tc_forward(int D, const __nv_bfloat16 *xcl, int N, int X, int Y, int Z, int cin,
+                            const __nv_bfloat16 *wpk, const float *bias, int cout, int relu, float *y, int *err,
+                            cudaStream_t st);
 
 namespace {
 
@@ -307,6 +318,14 @@ struct UNet {
   long long scratch_n = 0;
   double *dloss = nullptr;
   cudaStream_t st = nullptr;
+  // tensor-core inference: weights packed per layer in the MMA operand
+  // layout (offset -1: the layer runs on CUDA cores), the channels-last BF16
+  // copy of a layer's input, and the kernels' error word
+  __nv_bfloat16 *wpk = nullptr;
+  std::vector<long long> pk_off;
+  __nv_bfloat16 *xcl = nullptr;
+  long long xcl_n = 0;
+  int *terr = nullptr;
 };
 
 static long long vox(const UNet &u, int lvl) {
@@ -342,6 +361,47 @@ static void unet_layers(UNet &u) {
   }
   add(u.base, u.cout, 1);
   u.nparam = off;
+}
+
+// offsets of the packed tensor-core weights per layer (-1: CUDA cores); total
+// BF16 elements
+static long long tc_layout(UNet &u) {
+  long long off = 0;
+  u.pk_off.assign(u.layers.size(), -1);
+  for (size_t q = 0; q < u.layers.size(); ++q) {
+    const Layer &L = u.layers[q];
+    if (!conv_tc_supported(L.k, L.cout)) continue;
+    u.pk_off[q] = off;
+    const long long taps = u.D == 3 ? 27 : 9;
+    off += taps * conv_tc_cinp(L.cin) * L.cout;
+  }
+  return off;
+}
+
+// repack the BF16 weights for the tensor cores (after every weight change)
+static void tc_pack(UNet &u) {
+  for (size_t q = 0; q < u.layers.size(); ++q) {
+    if (u.pk_off[q] < 0) continue;
+    const Layer &L = u.layers[q];
+    conv_tc_pack_weights(u.wb + L.woff, L.cin, L.cout, u.D == 3 ? 27 : 9, u.wpk + u.pk_off[q], u.st);
+  }
+}
+
+// BF16 elements of the largest channels-last layer input at shape (N, X, Y, Z)
+static long long tc_xcl_elems(const UNet &u, int N, int X, int Y, int Z) {
+  long long best = 0;
+  int li = 0;
+  auto lvl_vox = [&](int l) {
+    long long v = (long long)(X >> l) * (Y >> l);
+    return u.D == 3 ? v * (Z >> l) : v;
+  };
+  for (int l = 0; l < u.levels; ++l)
+    for (int r = 0; r < 2; ++r, ++li)
+      if (u.pk_off[li] >= 0) best = std::max(best, (long long)N * lvl_vox(l) * conv_tc_cinp(u.layers[li].cin));
+  for (int l = u.levels - 2; l >= 0; --l)
+    for (int r = 0; r < 2; ++r, ++li)
+      if (u.pk_off[li] >= 0) best = std::max(best, (long long)N * lvl_vox(l) * conv_tc_cinp(u.layers[li].cin));
+  return best;
 }
 
 }  // namespace ep
@@ -385,6 +445,10 @@ static cudaError_t ensure_shape(UNet &u, int N, int X, int Y, int Z) {
   if (e == cudaSuccess) e = cudaMalloc((void **)&u.scratch, big * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc((void **)&u.scratch2, big * sizeof(float));
   u.scratch_n = big;
+  if (u.xcl) cudaFree(u.xcl);
+  u.xcl = nullptr;
+  u.xcl_n = tc_xcl_elems(u, N, X, Y, Z);
+  if (e == cudaSuccess && u.xcl_n > 0) e = cudaMalloc((void **)&u.xcl, u.xcl_n * sizeof(__nv_bfloat16));
   return e;
 }
 
@@ -409,9 +473,25 @@ static Idx indices(const UNet &u) {
   return I;
 }
 
+// one convolution on the tensor cores: the input to channels-last BF16, then
+// the implicit GEMM (the caller has checked that the layer is supported)
 template <int D>
-static void conv_fwd(UNet &u, const Layer &L, const float *x, float *y, int lvl, int relu) {
+static void conv_tc(const UNet &u, int li, int N, int X, int Y, int Z, const float *x, float *y, int relu,
+                    __nv_bfloat16 *xcl) {
+  const Layer &L = u.layers[li];
+  const long long nv = (long long)X * Y * Z;
+  conv_tc_to_channels_last(x, N, L.cin, nv, conv_tc_cinp(L.cin), xcl, u.st);
+  conv_tc_forward(D, xcl, N, X, Y, Z, L.cin, u.wpk + u.pk_off[li], u.w + L.boff, L.cout, relu, y, u.terr, u.st);
+}
+
+template <int D>
+static void conv_fwd(UNet &u, const Layer &L, const float *x, float *y, int lvl, int relu, bool tc = false) {
   const long long nv = vox(u, lvl);
+  const int li = (int)(&L - u.layers.data());
+  if (tc && u.pk_off[li] >= 0) {
+    conv_tc<D>(u, li, u.N, u.X >> lvl, u.Y >> lvl, D == 3 ? (u.Z >> lvl) : 1, x, y, relu, u.xcl);
+    return;
+  }
   dim3 grid(nblk(nv), (L.cout + 7) / 8, u.N);
   const int X = u.X >> lvl, Y = u.Y >> lvl, Z = D == 3 ? (u.Z >> lvl) : 1;
   if (L.k == 3)
@@ -446,13 +526,13 @@ static void relu_bwd(UNet &u, int q) {
 }
 
 template <int D>
-static void forward(UNet &u, const float *x) {
+static void forward(UNet &u, const float *x, bool tc = false) {
   const Idx I = indices(u);
   int li = 0;
   const float *in = x;
   for (int l = 0; l < u.levels; ++l) {
-    conv_fwd<D>(u, u.layers[li++], in, u.act[I.e0[l]], l, 1);
-    conv_fwd<D>(u, u.layers[li++], u.act[I.e0[l]], u.act[I.e1[l]], l, 1);
+    conv_fwd<D>(u, u.layers[li++], in, u.act[I.e0[l]], l, 1, tc);
+    conv_fwd<D>(u, u.layers[li++], u.act[I.e0[l]], u.act[I.e1[l]], l, 1, tc);
     if (l < u.levels - 1) {
       const int X = u.X >> l, Y = u.Y >> l, Z = D == 3 ? (u.Z >> l) : 1;
       long long n = (long long)u.N * u.act_c[I.pool[l]] * vox(u, l + 1);
@@ -468,8 +548,8 @@ static void forward(UNet &u, const float *x) {
     k_up<D><<<nblk((long long)u.N * cup * nv), NT, 0, u.st>>>(prev, u.act[I.cat[l]], u.N, cup, cup + c, 0, X, Y, Z);
     k_slot_copy<<<nblk((long long)u.N * c * nv), NT, 0, u.st>>>(u.act[I.e1[l]], u.act[I.cat[l]], u.N, c, c, 0,
                                                                 cup + c, cup, nv, 0);
-    conv_fwd<D>(u, u.layers[li++], u.act[I.cat[l]], u.act[I.d0[l]], l, 1);
-    conv_fwd<D>(u, u.layers[li++], u.act[I.d0[l]], u.act[I.d1[l]], l, 1);
+    conv_fwd<D>(u, u.layers[li++], u.act[I.cat[l]], u.act[I.d0[l]], l, 1, tc);
+    conv_fwd<D>(u, u.layers[li++], u.act[I.d0[l]], u.act[I.d1[l]], l, 1, tc);
     prev = u.act[I.d1[l]];
   }
   conv_fwd<D>(u, u.layers[li++], prev, u.act[I.out], 0, 0);
@@ -566,6 +646,18 @@ static ep_status nfail(ep_net *n, ep_status st, const std::string &m) {
     if (e_ != cudaSuccess) return nfail((n), EP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
+// the tensor-core kernels' error word: a bounded wait that ran out
+static ep_status tc_status(ep_net *n) {
+  int e = 0;
+  NCK(n, cudaMemcpyAsync(&e, n->u.terr, sizeof(int), cudaMemcpyDeviceToHost, n->u.st));
+  NCK(n, cudaStreamSynchronize(n->u.st));
+  if (e) {
+    cudaMemsetAsync(n->u.terr, 0, sizeof(int), n->u.st);
+    return nfail(n, EP_ERR_TIMEOUT, "tensor-core convolution: a bounded wait gave up");
+  }
+  return EP_OK;
+}
+
 static bool shape_ok(const ep_net *n, const int size[3]) {
   const int m = 1 << (n->u.levels - 1);
   for (int d = 0; d < n->u.D; ++d)
@@ -639,12 +731,22 @@ static long long static_layout(const UNet &u, const Shp &s, long long *off) {
     add(c, l);
     add(c, l);
   }
+  // the channels-last BF16 input of the tensor-core convolutions (two per
+  // float), at the index of the head output (which is written to y)
+  if (off) off[q] = total;
+  total += (tc_xcl_elems(u, s.N, s.X, s.Y, s.Z) / 2 + 64) / 64 * 64;
   return total;
 }
 
 template <int D>
-static void conv_fwd_s(const UNet &u, const Shp &s, const Layer &L, const float *x, float *y, int lvl, int relu) {
+static void conv_fwd_s(const UNet &u, const Shp &s, const Layer &L, const float *x, float *y, int lvl, int relu,
+                       __nv_bfloat16 *xcl) {
   const long long nv = svox(u, s, lvl);
+  const int li = (int)(&L - u.layers.data());
+  if (u.pk_off[li] >= 0) {
+    conv_tc<D>(u, li, s.N, s.X >> lvl, s.Y >> lvl, D == 3 ? (s.Z >> lvl) : 1, x, y, relu, xcl);
+    return;
+  }
   dim3 grid(nblk(nv), (L.cout + 7) / 8, s.N);
   const int X = s.X >> lvl, Y = s.Y >> lvl, Z = D == 3 ? (s.Z >> lvl) : 1;
   if (L.k == 3)
@@ -660,11 +762,12 @@ static void conv_fwd_s(const UNet &u, const Shp &s, const Layer &L, const float 
 template <int D>
 static void forward_static(const UNet &u, const Shp &s, const float *x, float *act, const long long *off, float *y) {
   const Idx I = indices(u);
+  __nv_bfloat16 *xcl = reinterpret_cast<__nv_bfloat16 *>(act + off[I.out]);
   int li = 0;
   const float *in = x;
   for (int l = 0; l < u.levels; ++l) {
-    conv_fwd_s<D>(u, s, u.layers[li++], in, act + off[I.e0[l]], l, 1);
-    conv_fwd_s<D>(u, s, u.layers[li++], act + off[I.e0[l]], act + off[I.e1[l]], l, 1);
+    conv_fwd_s<D>(u, s, u.layers[li++], in, act + off[I.e0[l]], l, 1, xcl);
+    conv_fwd_s<D>(u, s, u.layers[li++], act + off[I.e0[l]], act + off[I.e1[l]], l, 1, xcl);
     if (l < u.levels - 1) {
       const int X = s.X >> l, Y = s.Y >> l, Z = D == 3 ? (s.Z >> l) : 1;
       const long long n = (long long)s.N * (u.base << l) * svox(u, s, l + 1);
@@ -682,11 +785,11 @@ static void forward_static(const UNet &u, const Shp &s, const float *x, float *a
     k_up<D><<<nblk((long long)s.N * cup * nv), NT, 0, u.st>>>(prev, cat, s.N, cup, cup + c, 0, X, Y, Z);
     k_slot_copy<<<nblk((long long)s.N * c * nv), NT, 0, u.st>>>(act + off[I.e1[l]], cat, s.N, c, c, 0, cup + c, cup,
                                                                 nv, 0);
-    conv_fwd_s<D>(u, s, u.layers[li++], cat, act + off[I.d0[l]], l, 1);
-    conv_fwd_s<D>(u, s, u.layers[li++], act + off[I.d0[l]], act + off[I.d1[l]], l, 1);
+    conv_fwd_s<D>(u, s, u.layers[li++], cat, act + off[I.d0[l]], l, 1, xcl);
+    conv_fwd_s<D>(u, s, u.layers[li++], act + off[I.d0[l]], act + off[I.d1[l]], l, 1, xcl);
     prev = act + off[I.d1[l]];
   }
-  conv_fwd_s<D>(u, s, u.layers[li++], prev, y, 0, 0);
+  conv_fwd_s<D>(u, s, u.layers[li++], prev, y, 0, 0, xcl);
 }
 
 extern "C" {
@@ -724,10 +827,18 @@ ep_status ep_net_create(int ndim, int in_ch, int out_ch, int base, int levels, u
     ep_net_destroy(n);
     return nfail(nullptr, EP_ERR_OOM, "ep_net_create: allocation failed");
   }
+  const long long npk = tc_layout(u);
+  if ((npk > 0 && cudaMalloc((void **)&u.wpk, npk * sizeof(__nv_bfloat16)) != cudaSuccess) ||
+      cudaMalloc((void **)&u.terr, sizeof(int)) != cudaSuccess) {
+    ep_net_destroy(n);
+    return nfail(nullptr, EP_ERR_OOM, "ep_net_create: allocation failed");
+  }
+  cudaMemset(u.terr, 0, sizeof(int));
   cudaMemcpy(u.w, w.data(), np * 4, cudaMemcpyHostToDevice);
   cudaMemset(u.m, 0, np * 4);
   cudaMemset(u.v, 0, np * 4);
   k_to_bf16<<<nblk(np), NT, 0, u.st>>>(u.w, u.wb, np);
+  tc_pack(u);
   if (cudaStreamSynchronize(u.st) != cudaSuccess) {
     ep_net_destroy(n);
     return nfail(nullptr, EP_ERR_CUDA, "ep_net_create: initialisation failed");
@@ -752,6 +863,7 @@ ep_status ep_net_set_params(ep_net *n, const float *host, long long count) {
   if (!n || !host || count != n->u.nparam) return nfail(n, EP_ERR_ARG, "ep_net_set_params: bad arguments");
   NCK(n, cudaMemcpy(n->u.w, host, count * 4, cudaMemcpyHostToDevice));
   k_to_bf16<<<nblk(count), NT, 0, n->u.st>>>(n->u.w, n->u.wb, count);
+  tc_pack(n->u);
   NCK(n, cudaStreamSynchronize(n->u.st));
   return EP_OK;
 }
@@ -761,11 +873,11 @@ ep_status ep_net_forward(ep_net *n, const float *x, int N, const int size[3], fl
     return nfail(n, EP_ERR_ARG, "ep_net_forward: sizes must be multiples of 2^(levels-1)");
   UNet &u = n->u;
   NCK(n, ensure_shape(u, N, size[0], size[1], u.D == 3 ? size[2] : 1));
-  if (u.D == 2) forward<2>(u, x); else forward<3>(u, x);
+  if (u.D == 2) forward<2>(u, x, true); else forward<3>(u, x, true);
   const long long no = (long long)N * u.cout * vox(u, 0);
   NCK(n, cudaMemcpyAsync(y, u.act[indices(u).out], no * 4, cudaMemcpyDeviceToDevice, u.st));
   NCK(n, cudaGetLastError());
-  return EP_OK;
+  return tc_status(n);
 }
 
 // See the declaration in ep.h and the notes above g_static_act.
@@ -787,7 +899,7 @@ ep_status ep_net_forward_static(ep_net *n, const float *x, int N, const int size
   if (u.D == 2) forward_static<2>(u, s, x, act, off, y);
   else forward_static<3>(u, s, x, act, off, y);
   NCK(n, cudaGetLastError());
-  return EP_OK;
+  return tc_status(n);
 }
 
 static ep_status net_grads(ep_net *n, const float *x, const float *t, int N, const int size[3], double *loss) {
@@ -827,6 +939,7 @@ ep_status ep_net_train_step(ep_net *n, const float *x, const float *t, int N, co
   const float b1 = 0.9f, b2 = 0.999f;
   const float c1 = 1.f - powf(b1, (float)u.step), c2 = 1.f - powf(b2, (float)u.step);
   k_adam<<<nblk(u.nparam), NT, 0, u.st>>>(u.w, u.wb, u.g, u.m, u.v, u.nparam, lr, b1, b2, 1e-8f, c1, c2);
+  tc_pack(u);
   NCK(n, cudaGetLastError());
   NCK(n, cudaStreamSynchronize(u.st));
   return EP_OK;
@@ -840,6 +953,7 @@ ep_status ep_net_destroy(ep_net *n) {
   for (float *p : u.grad) cudaFree(p);
   cudaFree(u.scratch); cudaFree(u.scratch2);
   cudaFree(u.w); cudaFree(u.g); cudaFree(u.m); cudaFree(u.v); cudaFree(u.wb); cudaFree(u.dloss);
+  cudaFree(u.wpk); cudaFree(u.xcl); cudaFree(u.terr);
   delete n;
   return EP_OK;
 }

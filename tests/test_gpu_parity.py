@@ -417,6 +417,74 @@ def test_not_converged_keeps_state_and_reports(P):
     g.commit_increment()
 
 
+def test_nan_in_the_history_is_reported_as_diverged_and_the_grid_recovers(P):
+    """Failure injection on the host (SURVEY's failure-detection plan, no GPU
+    fault): a NaN written into the old stress through ep_set_fields reaches
+    the residual norms, the solve returns EP_ERR_DIVERGED without
+    committing, and the handle stays usable: with the finite history put
+    back, the increment solves as on a grid that never saw the NaN.  A NaN
+    cohesion is refused on the host."""
+    s = E.config(1, n=(32, 28))
+    g = gpu_grid(P, s, P.FP64)
+    ref = gpu_grid(P, s, P.FP64)
+    for _ in range(4):
+        for x in (g, ref):
+            x.apply_increment(1.0, s.dt, P.LOAD_XY)
+            x.solve_increment()
+    txx = g.get("txx")
+    bad = txx.copy()
+    bad[14, 16] = np.nan
+    g.set("txx", bad)
+    g.apply_increment(1.0, s.dt, P.LOAD_XY)
+    info = g.solve_increment(raise_on_fail=False)
+    assert info["status"] == 6, info            # EP_ERR_DIVERGED
+    assert np.isnan(g.get("txx")[14, 16])       # nothing committed
+    g.set("txx", txx)
+    g.apply_increment(1.0, s.dt, P.LOAD_XY)
+    ig = g.solve_increment()
+    ref.apply_increment(1.0, s.dt, P.LOAD_XY)
+    ir = ref.solve_increment()
+    assert ig["iters"] == ir["iters"]
+    for f in FIELDS_2D:
+        assert np.array_equal(g.get(f), ref.get(f)), f
+    coh = s.cohesion()
+    coh.ravel()[5] = np.nan
+    with pytest.raises(P.EPError, match="not finite"):
+        g.set_material(s.K, s.G, s.mu_s, s.phi_deg, s.psi_deg, coh)
+    g.close()
+    ref.close()
+
+
+def test_tma_wait_that_runs_out_ends_the_solve_with_timeout(P):
+    """A bounded device wait made to run out (the TMA sweep's plane-copy
+    waits given a bound of 8 cycles, far below a copy's latency): the
+    kernel records the timeout, waits with its default bound for the copies
+    it issued and returns; the solve ends with EP_ERR_TIMEOUT, and with the
+    default bound back the same increment solves as on an untouched grid."""
+    s = E.config(3, n=(20, 17, 14), inclusion_radius=0.2, tol=1e-9)
+    g = gpu_grid(P, s, P.FP64)
+    ref = gpu_grid(P, s, P.FP64)
+    for x in (g, ref):
+        x.set_kernel(P.KERNEL_FUSED_TMA, 0)
+        for _ in range(4):
+            x.apply_increment_rates(rates_of(s), s.dt)
+            x.solve_increment()
+    g.set_solver(tol=s.tol, wait_cycles=8)
+    g.apply_increment_rates(rates_of(s), s.dt)
+    info = g.solve_increment(raise_on_fail=False)
+    assert info["status"] == 7, info            # EP_ERR_TIMEOUT
+    g.set_solver(tol=s.tol)
+    g.apply_increment_rates(rates_of(s), s.dt)
+    ig = g.solve_increment()
+    ref.apply_increment_rates(rates_of(s), s.dt)
+    ir = ref.solve_increment()
+    assert ig["iters"] == ir["iters"] and ir["n_plastic"] > 0
+    for f in FIELDS_3D:
+        assert np.array_equal(g.get(f), ref.get(f)), f
+    g.close()
+    ref.close()
+
+
 def test_argument_and_state_errors(P):
     with pytest.raises(P.EPError):
         P.Grid(2, (0, 5))
@@ -722,3 +790,118 @@ def test_frozen_plasticity_fp64_parity_2d_batched(P, tile):
 def test_frozen_plasticity_fp64_parity_3d(P, variant):
     s = E.config(3, n=(20, 17, 14), tol=1e-9, precision="fp64", inclusion_radius=0.2)
     assert run_frozen_pair(P, s, 7, variant=variant, kz=5) >= 1
+
+
+# ------------------------------------------------- incompressible (NEXT-3) --
+@pytest.mark.parametrize("kernel", [("staged", 0), ("strips", 1)])
+def test_incompressible_fp64_parity_2d(P, kernel):
+    """The incompressible variant (Eq. A2ssP2 in place of Eq. A2ssP: the
+    pressure is pseudo-time state stepped by -K~ div v, starting at the old
+    pressure; reading R9) against the oracle's: same iterations and fields
+    within 1e-10 through first yield of an inclusion, with the staged sweep
+    and with the fused warp strips."""
+    s = E.config(1, n=(40, 33), tol=1e-9)
+    g = gpu_grid(P, s, P.FP64, incompressible=True)
+    if kernel[1]:
+        g.set_kernel(P.KERNEL_FUSED, 3)
+    else:
+        g.set_kernel(P.KERNEL_STAGED, -1)
+    o = O.from_setup(s, incompressible=True)
+    for inc in range(1, 9):
+        g.apply_increment_rates(rates_of(s), s.dt)
+        ig = g.solve_increment()
+        o.apply_increment(rates_of(s), s.dt)
+        io = o.solve_increment()
+        assert ig["iters"] == io["iters"], (inc, ig["iters"], io["iters"])
+        sc = group_scales(o, FIELDS_2D)
+        for f in FIELDS_2D:
+            e = rel_err(g.get(f), o.get(f), sc[f])
+            assert e <= 1e-10, (inc, f, e)
+    assert io["n_plastic"] > 0
+    g.close()
+
+
+@pytest.mark.parametrize("variant", [0, 3])
+def test_incompressible_fp64_parity_3d(P, variant):
+    """The same in 3D (x-z pure shear) with the staged sweep and the register
+    z-march kernel."""
+    s = E.config(3, n=(17, 13, 11), inclusion_radius=0.25, tol=1e-9)
+    g = gpu_grid(P, s, P.FP64, incompressible=True)
+    g.set_kernel(variant, 4 if variant else -1)
+    o = O.from_setup(s, incompressible=True)
+    for inc in range(1, 7):
+        g.apply_increment_rates(rates_of(s), s.dt)
+        ig = g.solve_increment()
+        o.apply_increment(rates_of(s), s.dt)
+        io = o.solve_increment()
+        assert ig["iters"] == io["iters"], (inc, ig["iters"], io["iters"])
+        sc = group_scales(o, FIELDS_3D)
+        for f in FIELDS_3D:
+            e = rel_err(g.get(f), o.get(f), sc[f])
+            assert e <= 1e-10, (inc, f, e)
+    assert io["n_plastic"] > 0
+    g.close()
+
+
+def test_incompressible_fp32_within_stated_bounds_3d(P):
+    """FP32 sweeps of the incompressible variant against the FP64 oracle:
+    stress within 1e-5 and plastic strain within 1e-4."""
+    s = E.config(3, n=(16, 15, 14), inclusion_radius=0.2)
+    worst = run_fp32_vs_oracle(P, s, 7, incompressible=True)
+    for f in ("txx", "tyy", "tzz", "txy", "txz", "tyz", "p"):
+        assert worst[f] <= 1e-5, (f, worst[f])
+    assert worst["epl"] <= 1e-4, worst["epl"]
+    assert worst["epl_max"] > 0
+
+
+# ------------------------------------- per-cell shear modulus (NEXT-2) -----
+@pytest.mark.parametrize("nd,mu_s", [(2, math.inf), (2, 2e-3), (3, math.inf)])
+def test_per_cell_shear_modulus_fp64_parity(P, nd, mu_s):
+    """The paper's heterogeneous box (Sec. 4.1: Gaussian G-bar and c-bar with
+    the wall jump; reading R10 for where a per-cell G enters) against the
+    oracle with the same per-cell modulus: same iterations and fields within
+    1e-10 through first yield, in the elastic limit and with a Maxwell
+    viscosity (which makes the weight c2 of the rotated old stress vary from
+    point to point)."""
+    n = (40, 33) if nd == 2 else (16, 13, 11)
+    s = E.gaussian_setup(nd, n=n, mu_s=mu_s, tol=1e-9)
+    g = gpu_grid(P, s, P.FP64)
+    g.set_shear_modulus(s.shear_modulus())
+    o = O.from_setup(s)
+    o.set_shear_modulus(s.shear_modulus())
+    fields = FIELDS_2D if nd == 2 else FIELDS_3D
+    for inc in range(1, 12 if nd == 2 else 14):
+        g.apply_increment_rates(rates_of(s), s.dt)
+        ig = g.solve_increment()
+        o.apply_increment(rates_of(s), s.dt)
+        io = o.solve_increment()
+        assert ig["iters"] == io["iters"], (inc, ig["iters"], io["iters"])
+        sc = group_scales(o, fields)
+        for f in fields:
+            e = rel_err(g.get(f), o.get(f), sc[f])
+            assert e <= 1e-10, (inc, f, e)
+    assert io["n_plastic"] > 0
+    g.close()
+
+
+def test_per_cell_shear_modulus_fp32_within_stated_bounds(P):
+    """FP32 sweeps on the heterogeneous 2D box against the FP64 oracle:
+    stress within 1e-5, plastic strain within 1e-4."""
+    s = E.gaussian_setup(2, n=(48, 40), tol=1e-6)
+    g = gpu_grid(P, s, P.FP32_MIXED, tol=1e-6, max_iter=400000)
+    g.set_shear_modulus(s.shear_modulus())
+    o = O.from_setup(s, tol=1e-10)
+    o.set_shear_modulus(s.shear_modulus())
+    worst = {}
+    for inc in range(1, 12):
+        g.apply_increment_rates(rates_of(s), s.dt)
+        g.solve_increment()
+        o.apply_increment(rates_of(s), s.dt)
+        o.solve_increment()
+        sc = group_scales(o, FIELDS_2D)
+        for f in FIELDS_2D:
+            worst[f] = max(worst.get(f, 0.0), rel_err(g.get(f), o.get(f), sc[f]))
+    for f in ("txx", "tyy", "txy", "p"):
+        assert worst[f] <= 1e-5, (f, worst[f])
+    assert worst["epl"] <= 1e-4 and o.get("epl").max() > 0, worst["epl"]
+    g.close()

@@ -69,6 +69,54 @@ def test_net_forward_and_gradient_match_oracle(P, nd, shape, base, levels):
     net.close()
 
 
+@pytest.mark.parametrize("nd,shape,base,levels,N", [(2, (36, 20), 16, 3, 2), (3, (12, 8, 20), 16, 2, 1),
+                                                    (3, (16, 16, 16), 32, 3, 1)])
+def test_tensor_core_forward_matches_the_bf16_input_oracle(P, nd, shape, base, levels, N):
+    """The inference forward, whose 3^D convolutions with 16..128 output
+    channels run as tcgen05 implicit GEMMs (BF16 inputs from TMA boxes, FP32
+    accumulation in tensor memory), against the FP64 numpy network with the
+    same BF16 rounding of those convolutions' inputs, on the warm start's
+    channel counts (input channels padded to 16) and shapes whose bricks are
+    ragged; the training forward (FP32 on CUDA cores) is checked through the
+    loss against the unrounded network."""
+    import torch
+    cin, cout = P.warm_in(nd), P.warm_out(nd)
+    net = P.Net(nd, cin, cout, base=base, levels=levels, seed=13)
+    table, _ = U.layer_table(nd, cin, cout, base, levels)
+    rng = np.random.default_rng(8)
+    params = net.get_params().astype(np.float64)
+    for (ci, co, k, wo, bo) in table:
+        params[bo:bo + co] = rng.normal(size=co) * 0.05
+    ci, co, k, wo, bo = table[-1]
+    params[wo:wo + ci * co] = rng.normal(size=ci * co) * 0.3
+    net.set_params(params.astype(np.float32))
+    pk = params.copy()
+    for (ci, co, k, wo, bo) in table:
+        pk[wo:wo + ci * co * k ** nd] = _bf16(params[wo:wo + ci * co * k ** nd])
+        pk[bo:bo + co] = params[bo:bo + co].astype(np.float32)
+    dims = tuple(reversed(shape))
+    x = rng.normal(size=(N, cin) + dims).astype(np.float32)
+    t = rng.normal(size=(N, cout) + dims).astype(np.float32)
+    xg = torch.tensor(x, device="cuda").contiguous()
+    tg = torch.tensor(t, device="cuda").contiguous()
+    yg = torch.full((N, cout) + dims, float("nan"), dtype=torch.float32, device="cuda")
+    net.forward(xg.data_ptr(), N, list(shape), yg.data_ptr())
+    torch.cuda.synchronize()
+    y = yg.cpu().numpy().astype(np.float64)
+    y_bf = U.forward(pk, x.astype(np.float64), nd, cin, cout, base, levels, bf16_inputs=True)
+    y_fp = U.forward(pk, x.astype(np.float64), nd, cin, cout, base, levels)
+    scale = np.abs(y_bf).max()
+    err_bf = np.abs(y - y_bf).max() / scale
+    err_fp = np.abs(y - y_fp).max() / scale
+    assert np.isfinite(y).all() and scale > 0
+    assert err_bf <= 2e-3, (err_bf, err_fp)
+    assert err_bf < err_fp or err_fp <= 2e-3        # the rounding model explains the difference
+    loss = net.loss(xg.data_ptr(), tg.data_ptr(), N, list(shape))
+    ref = U.loss(pk, x.astype(np.float64), t.astype(np.float64), nd, cin, cout, base, levels)
+    assert abs(loss - ref) <= 1e-4 * ref
+    net.close()
+
+
 def _lockstep(P, s, incs, coarsens):
     """A GPU FP64 grid and the oracle through `incs` increments; then the
     GPU's features before the next increment and its targets after it,

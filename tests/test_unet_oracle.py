@@ -52,3 +52,11 @@ def test_fd_gradient_of_a_quadratic_is_exact():
     # dL/db_c = 2 sum_{n,y,x} (y - t)[n, c] / numel = 2 mean_c(y - t) / C
     analytic = 2 * (y - t).mean(axis=(0, 2, 3)) / y.shape[1]
     np.testing.assert_allclose(g[bo:bo + 2], analytic, rtol=1e-6)
+
+
+def test_bf16_rounding_is_nearest_even():
+    """round_bf16 keeps 8 significant bits, rounding to nearest with ties to
+    even (the conversion the tensor-core forward applies to its inputs)."""
+    x = np.array([1.0, 1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, 1.0 + 2.0 ** -9, -2.5, 1.0 + 2.0 ** -7 + 2.0 ** -12])
+    y = U.round_bf16(x)
+    np.testing.assert_array_equal(y, [1.0, 1.0, 1.0 + 2.0 ** -6, 1.0, -2.5, 1.0 + 2.0 ** -7])
