@@ -55,6 +55,10 @@ def parse():
     ap.add_argument("--increment", type=int, default=5, help="first increment of the timed sequence")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 increment")
     ap.add_argument("--no-warm", action="store_true", help="plain start instead of the learned warm start")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
+                    help="precision of the stepped walk (fp64: plain start, for profiling the FP64 sweep)")
+    ap.add_argument("--no-increments", action="store_true",
+                    help="skip the whole-increment arms (for short profiling runs)")
     ap.add_argument("--coarsen", type=int, default=0,
                     help="fine cells per coarse cell side of the network's grid (0: size / 64)")
     ap.add_argument("--train-size", type=int, default=127, help="box of the training trajectories")
@@ -377,8 +381,14 @@ def aggregate(torch, dist, seconds, units, device):
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # dominant kernel from one ncu capture of the benchmark command, by kernel and
 # box size; the entry must be dropped when the kernel changes.
-NCU_TRAFFIC = {("k_fused3d_reg", 127): 271.8e6}
-NCU_SOURCE = {("k_fused3d_reg", 127): "ncu --set full capture of one launch at 127^3 (profiles/)"}
+NCU_TRAFFIC = {("k_fused3d_reg", 127): 270.2e6,
+               ("k_fused3d_reg", 511): 270.2e6 * 133432831 / 2048383}
+NCU_SOURCE = {("k_fused3d_reg", 127): "ncu --set full capture of one launch at 127^3 (profiles/)",
+              ("k_fused3d_reg", 511): "ncu --set full capture of one launch at 127^3 (profiles/), the per-cell "
+                                      "traffic scaled to 511^3 by the cell count"}
+# FP64 flops per cell of one staged FP64 sweep (dadd + dmul + 2 dfma thread
+# instructions of its five kernels, counted by ncu at 127^3; profiles/)
+FP64_FLOPS_PER_CELL = 322.5
 # the survey's algorithmic bytes per cell of a 3D FP32 sweep whose stress is
 # no pseudo-time state (reported beside the fraction by the scheme's bytes)
 SURVEY_BYTES_3D_FP32 = 80.0
@@ -441,14 +451,16 @@ def train_warm(args, torch, P, stream):
         iters.append(W.collect(gt, ts.a, ts.dt, incs, data, load_plane=P.LOAD_XZ, coarsen=f_tr))
         gt.close()
         groups.append(data)
-    zero = W.zero_loss(groups)
+    scale = W.calibrate(net, groups)     # losses below in units of the targets' RMS
+    zero = W.zero_loss(net, groups)
     before = W.evaluate(net, groups)
-    W.train(net, groups, steps=args.warm_steps, lr=1e-3, batch=2)
+    W.train(net, groups, steps=args.warm_steps, lr=1e-3, batch=2, calibrate_scale=False)
     torch.cuda.synchronize()
     after = W.evaluate(net, groups)
     info = {"net": "3-level U-Net, base %d, BF16 weights, FP32 accumulation" % args.warm_base,
             "train_box": "%d^3, coarse cells of %d^3 fine cells (%s per side)" % (n_tr, f_tr, "x".join(map(str, dims[:3]))),
             "setups": args.warm_train, "samples": sum(d.n for d in groups), "steps": args.warm_steps,
+            "output_scale": scale, "loss_unit": "mean square of the training targets",
             "train_mse_before": before, "train_mse_after": after, "train_mse_zero_net": zero,
             "train_iterations": iters, "seconds": time.perf_counter() - t0}
     return net, info
@@ -499,10 +511,13 @@ def our_arm(args):
     s = setup_for(args.size, args.tol)
     cells = s.n[0] * s.n[1] * s.n[2]
     nchk = check_interval(s.n[0], "fp32")
+    if args.precision == "fp64":
+        args.no_warm = True
+        nchk = check_interval(s.n[0], "fp64")
     net, training = (None, None) if args.no_warm else train_warm(args, torch, P, stream)
 
     # the benchmark box: the increments before the timed one, then a checkpoint
-    g = prepare(P, s, "fp32", args.increment, args.kernel, stream.cuda_stream)
+    g = prepare(P, s, args.precision, args.increment, args.kernel, stream.cuda_stream, nchk=nchk)
     if net is not None:
         g.attach_warm_start(net, args.coarsen)
     bpc = g.sweep_bytes_per_cell()
@@ -530,17 +545,17 @@ def our_arm(args):
     fields_out = ["vx", "vy", "vz", "txx", "tyy", "tzz", "txy", "txz", "tyz", "p", "epl"]
     g.restore()
     host = {"in": {}, "out": {}}
-    for f in fields_in:
+    for f in ([] if args.no_increments else fields_in):
         b = torch.empty(g.count(f), dtype=torch.float64, pin_memory=True)
         g.get_into(f, b.data_ptr(), b.numel())
         host["in"][f] = b
-    for f in fields_out:
+    for f in ([] if args.no_increments else fields_out):
         host["out"][f] = torch.empty(g.count(f), dtype=torch.float64, pin_memory=True)
     h2d = sum(b.numel() * 8 for b in host["in"].values()) + 8 * 4
     d2h = sum(b.numel() * 8 for b in host["out"].values())
     arms = {}
     for name, warm in (("warm_fp32", net is not None), ("plain_fp32", False)):
-        if name == "warm_fp32" and net is None:
+        if (name == "warm_fp32" and net is None) or args.no_increments:
             continue
         dev_ms, wall, info = full_increment(torch, P, g, s, stream, barrier, warm,
                                             host if name == "warm_fp32" else None)
@@ -567,12 +582,19 @@ def our_arm(args):
         net.close()
 
     fp64 = None
-    if not args.no_fp64:
+    if not args.no_fp64 and not args.no_increments:
         g64 = prepare(P, s, "fp64", args.increment, "auto", stream.cuda_stream, nchk=nchk)
         dev_ms, _, i64 = full_increment(torch, P, g64, s, stream, barrier, False)
         fp64 = {"ms_per_increment": dev_ms, "iterations": i64["iters"], "frozen_at": i64["frozen_at"],
                 "kernel": "staged",
                 "GB_per_s": g64.sweep_bytes_per_cell() * cells * (i64["iters"] + 1) / (dev_ms * 1e-3) / 1e9}
+        # its roof is FP64 arithmetic: flops of the sweeps against the FMA
+        # rate measured on this device now
+        peak64 = P.measure_fp64_peak()
+        tf = FP64_FLOPS_PER_CELL * cells * (i64["iters"] + 1) / (dev_ms * 1e-3) / 1e12
+        fp64["roofline"] = {"bound": "fp64-alu", "achieved": tf, "peak": peak64, "unit": "TFLOP/s",
+                            "frac": tf / peak64, "flops_per_cell": FP64_FLOPS_PER_CELL,
+                            "peak_source": "measured (ep_measure_fp64_peak, FMA chains, 2 flops per FMA)"}
         for name in arms:
             arms[name]["speedup_vs_fp64"] = dev_ms / arms[name]["ms_per_increment"]
         g64.close()
@@ -604,9 +626,9 @@ def our_arm(args):
     line = {
         "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "3d-ep-xz-inclusion %d^3 (%d cells), increments from %d on, tol %g, fp32 sweeps, %s"
-                   % (s.n[0], cells, args.increment, args.tol, warm_desc),
+        "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": "3d-ep-xz-inclusion %d^3 (%d cells), increments from %d on, tol %g, %s sweeps, %s"
+                   % (s.n[0], cells, args.increment, args.tol, args.precision, warm_desc),
                    "step": "one chunk of %d pseudo-transient sweeps of the increment sequence (a new increment, "
                            "with its warm-start inference and start state, is opened by the step that needs it; "
                            "a converged one is committed by the step that decides it)" % nchk,

@@ -287,12 +287,21 @@ ep_status ep_net_forward(ep_net_handle n, const float *x, int N, const int size[
  * ep_net_forward. */
 #define EP_NET_STATIC_FLOATS (16LL * 1024 * 1024)
 ep_status ep_net_forward_static(ep_net_handle n, const float *x, int N, const int size[3], float *y);
-/* MSE loss mean((net(x) - t)^2) and its parameter gradient (host, nullable) */
+/* MSE loss mean(((net(x) - t)/scale)^2) (scale: ep_net_set_output_scale,
+ * default 1) and its parameter gradient (host, nullable) */
 ep_status ep_net_gradients(ep_net_handle n, const float *x, const float *t, int N, const int size[3],
                            double *loss, float *grad_host, long long count);
 /* one Adam step (beta 0.9 / 0.999) on the MSE loss; loss (nullable, host) */
 ep_status ep_net_train_step(ep_net_handle n, const float *x, const float *t, int N, const int size[3], float lr,
                             double *loss);
+/* The network's output is `scale` times its head's (default 1), and the
+ * training loss is taken in units of the scale: mean(((net(x) - t)/scale)^2).
+ * With the scale set to the training targets' root mean square the head's
+ * values, the loss and the gradients stay of order one whatever the targets'
+ * magnitude (Adam's epsilon then stays negligible).  0 makes the output zero
+ * and the loss the targets' mean square. */
+ep_status ep_net_set_output_scale(ep_net_handle n, double scale);
+ep_status ep_net_get_output_scale(ep_net_handle n, double *scale);
 ep_status ep_net_destroy(ep_net_handle n);
 const char *ep_net_last_error(ep_net_handle n);
 

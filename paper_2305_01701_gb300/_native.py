@@ -88,6 +88,8 @@ SIGNATURES = [
     ("ep_solve_chunks", _I, [_P, _I, C.POINTER(SolveInfo)]),
     ("ep_set_shear_modulus", _I, [_P, _DP]),
     ("ep_measure_fp64_peak", _I, [C.POINTER(C.c_double)]),
+    ("ep_net_set_output_scale", _I, [_P, _D]),
+    ("ep_net_get_output_scale", _I, [_P, C.POINTER(C.c_double)]),
     ("ep_commit_increment", _I, [_P]),
     ("ep_field_count", _I, [_P, _I, C.POINTER(C.c_size_t)]),
     ("ep_get_fields", _I, [_P, _I, _DP, _Z]),
@@ -467,6 +469,14 @@ class Net:
         gradient copy)."""
         out = C.c_double()
         _ncheck(self.h, self._L.ep_net_gradients(self.h, x_ptr, t_ptr, N, self._size(size), C.byref(out), None, 0))
+        return out.value
+
+    def set_output_scale(self, scale):
+        _ncheck(self.h, self._L.ep_net_set_output_scale(self.h, float(scale)))
+
+    def output_scale(self):
+        out = C.c_double()
+        _ncheck(self.h, self._L.ep_net_get_output_scale(self.h, C.byref(out)))
         return out.value
 
     def train_step(self, x_ptr, t_ptr, N, size, lr):

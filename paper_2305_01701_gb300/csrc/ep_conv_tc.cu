@@ -297,7 +297,10 @@ cudaError_t conv_tc_forward(int D, const __nv_bfloat16 *xcl, int N, int X, int Y
                             const __nv_bfloat16 *wpk, const float *bias, int cout, int relu, float *y, int *err,
                             cudaStream_t st) {
   static bool configured[2] = {false, false};
-  const size_t smem = sizeof(ConvSmem) + 1024;
+  // 1 KB for the alignment, and 24 KB of slack behind the operand buffers so
+  // that every operand address the descriptors can form stays inside the
+  // block's shared memory
+  const size_t smem = sizeof(ConvSmem) + 1024 + 24 * 1024;
   if (!configured[D - 2]) {
     cudaError_t e = D == 3 ? cudaFuncSetAttribute(k_conv_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
                            : cudaFuncSetAttribute(k_conv_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

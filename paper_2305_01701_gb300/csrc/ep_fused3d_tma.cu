@@ -80,8 +80,24 @@ __device__ __forceinline__ bool bar_try(unsigned long long *b, unsigned parity) 
 // bounded wait: gives up after `limit` SM cycles (by default 2^31, about
 // 1 s at 2 GHz, far above any copy's latency)
 constexpr long long WAIT_DEFAULT = 1ll << 31;
+// test_wait polls without suspending the thread, so that the bound, not
+// the hardware's own suspend window, decides when the wait gives up
+__device__ __forceinline__ bool bar_test(unsigned long long *b, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
 __device__ __forceinline__ bool bar_wait(unsigned long long *b, unsigned parity, long long limit = WAIT_DEFAULT) {
   const long long t0 = clock64();
+  if (limit < WAIT_DEFAULT) {
+    while (!bar_test(b, parity))
+      if (clock64() - t0 > limit) return false;
+    return true;
+  }
   while (!bar_try(b, parity))
     if (clock64() - t0 > limit) return false;
   return true;

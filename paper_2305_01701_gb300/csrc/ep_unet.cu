@@ -157,6 +157,11 @@ __global__ void k_conv_wgrad(const float *__restrict__ x, const float *__restric
   }
 }
 
+__global__ void k_scale(float *a, long long n, float s) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) a[t] *= s;
+}
+
 __global__ void k_relu_bwd(const float *a, float *g, long long n) {
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < n && a[t] <= 0.f) g[t] = 0.f;
@@ -257,11 +262,14 @@ __device__ __forceinline__ double block_sum_fixed(double v, double *sh) {
   return s;
 }
 
-__global__ void k_mse(const float *y, const float *t, float *g, long long n, double *partial) {
+// With an output scale s (y = s h), the loss is taken in units of s,
+// mean(((y - t) / s)^2), and g receives its gradient with respect to the
+// head's output h: 2 (y - t) / (s n).  inv_s = 1 / s (1 for s = 0 or 1).
+__global__ void k_mse(const float *y, const float *t, float *g, long long n, double *partial, float inv_s) {
   __shared__ double sh[NT / 32];
   double d2 = 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const float d = y[i] - t[i];
+    const float d = (y[i] - t[i]) * inv_s;
     g[i] = 2.f * d / (float)n;
     d2 += (double)d * d;
   }
@@ -326,6 +334,9 @@ struct UNet {
   __nv_bfloat16 *xcl = nullptr;
   long long xcl_n = 0;
   int *terr = nullptr;
+  // the network's output is out_scale times the head's: training on targets
+  // of any magnitude keeps the head's values of order one
+  float out_scale = 1.f;
 };
 
 static long long vox(const UNet &u, int lvl) {
@@ -553,6 +564,10 @@ static void forward(UNet &u, const float *x, bool tc = false) {
     prev = u.act[I.d1[l]];
   }
   conv_fwd<D>(u, u.layers[li++], prev, u.act[I.out], 0, 0);
+  if (u.out_scale != 1.f) {
+    const long long no = (long long)u.N * u.cout * vox(u, 0);
+    k_scale<<<nblk(no), NT, 0, u.st>>>(u.act[I.out], no, u.out_scale);
+  }
 }
 
 // gradients of all parameters given d loss / d out in u.grad[out]
@@ -790,6 +805,10 @@ static void forward_static(const UNet &u, const Shp &s, const float *x, float *a
     prev = act + off[I.d1[l]];
   }
   conv_fwd_s<D>(u, s, u.layers[li++], prev, y, 0, 0, xcl);
+  if (u.out_scale != 1.f) {
+    const long long no = (long long)s.N * u.cout * svox(u, s, 0);
+    k_scale<<<nblk(no), NT, 0, u.st>>>(y, no, u.out_scale);
+  }
 }
 
 extern "C" {
@@ -909,7 +928,8 @@ static ep_status net_grads(ep_net *n, const float *x, const float *t, int N, con
   const Idx I = indices(u);
   const long long no = (long long)N * u.cout * vox(u, 0);
   NCK(n, cudaMemsetAsync(u.g, 0, u.nparam * 4, u.st));
-  k_mse<<<MSE_BLOCKS, NT, 0, u.st>>>(u.act[I.out], t, u.grad[I.out], no, u.dloss + 1);
+  const float inv_s = u.out_scale > 0.f ? 1.f / u.out_scale : 1.f;
+  k_mse<<<MSE_BLOCKS, NT, 0, u.st>>>(u.act[I.out], t, u.grad[I.out], no, u.dloss + 1, inv_s);
   k_mse_final<<<1, NT, 0, u.st>>>(u.dloss + 1, no, u.dloss);
   if (u.D == 2) backward<2>(u, x); else backward<3>(u, x);
   NCK(n, cudaGetLastError());
@@ -942,6 +962,19 @@ ep_status ep_net_train_step(ep_net *n, const float *x, const float *t, int N, co
   tc_pack(u);
   NCK(n, cudaGetLastError());
   NCK(n, cudaStreamSynchronize(u.st));
+  return EP_OK;
+}
+
+ep_status ep_net_set_output_scale(ep_net *n, double scale) {
+  if (!n || !(scale >= 0.0) || !std::isfinite(scale))
+    return nfail(n, EP_ERR_ARG, "ep_net_set_output_scale: need a finite scale >= 0");
+  n->u.out_scale = (float)scale;
+  return EP_OK;
+}
+
+ep_status ep_net_get_output_scale(ep_net *n, double *scale) {
+  if (!n || !scale) return nfail(n, EP_ERR_ARG, "ep_net_get_output_scale: null argument");
+  *scale = n->u.out_scale;
   return EP_OK;
 }
 

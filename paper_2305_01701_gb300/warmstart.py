@@ -10,8 +10,7 @@ the relaxed-return part of its converged stress state (include/ep.h,
 ep_warm_features / ep_warm_target).  A network that outputs zero reproduces
 the plain start.  PyTorch only supplies the device buffers the library writes
 into; every arithmetic step of collection, training and inference runs in the
-library (`zero_loss` reduces the stored targets with torch, for the report
-only).
+library.
 """
 from __future__ import annotations
 
@@ -66,12 +65,25 @@ def collect(grid, a, dt, increments, samples, load_plane=LOAD_XY, coarsen=1, war
     return iters
 
 
-def train(net, groups, steps=400, lr=1e-3, batch=8, seed=0):
+def calibrate(net, groups):
+    """Set the network's output scale to the root mean square of the stored
+    targets (the library's loss of the network with its output scaled to
+    zero), so that its head, its loss and its gradients are of order one."""
+    net.set_output_scale(0.0)
+    ms = evaluate(net, groups)
+    net.set_output_scale(float(np.sqrt(ms)) if ms > 0 else 1.0)
+    return net.output_scale()
+
+
+def train(net, groups, steps=400, lr=1e-3, batch=8, seed=0, calibrate_scale=True):
     """Adam on the MSE loss over minibatches of consecutive samples of one
-    padded size (drawn at random); returns the loss history."""
+    padded size (drawn at random), after setting the output scale from the
+    targets (`calibrate`) unless told otherwise; returns the loss history."""
     rng = np.random.default_rng(seed)
     losses = []
     groups = [g for g in groups if g.n > 0]
+    if calibrate_scale:
+        calibrate(net, groups)
     for _ in range(steps):
         g = groups[rng.integers(len(groups))]
         nb = min(batch, g.n)
@@ -93,12 +105,11 @@ def evaluate(net, groups, batch=2):
     return total / max(count, 1)
 
 
-def zero_loss(groups):
-    """The same mean MSE for a network that outputs zero, i.e. for the plain
-    start (the warm start's fallback)."""
-    total, count = 0.0, 0
-    for g in groups:
-        if g.n:
-            total += float((g.t[:g.n].double() ** 2).mean()) * g.n
-            count += g.n
-    return total / max(count, 1)
+def zero_loss(net, groups):
+    """The same mean loss, in the network's units, for its output scaled to
+    zero, i.e. for the plain start (the warm start's fallback)."""
+    s = net.output_scale()
+    net.set_output_scale(0.0)
+    ms = evaluate(net, groups)
+    net.set_output_scale(s)
+    return ms / (s * s) if s > 0 else ms

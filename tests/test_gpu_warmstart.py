@@ -109,8 +109,11 @@ def test_tensor_core_forward_matches_the_bf16_input_oracle(P, nd, shape, base, l
     err_bf = np.abs(y - y_bf).max() / scale
     err_fp = np.abs(y - y_fp).max() / scale
     assert np.isfinite(y).all() and scale > 0
-    assert err_bf <= 2e-3, (err_bf, err_fp)
-    assert err_bf < err_fp or err_fp <= 2e-3        # the rounding model explains the difference
+    # FP32 accumulation in another order can move an intermediate value
+    # across a BF16 rounding boundary (one unit of 2^-8 relative), which the
+    # following layers carry on: a few 1e-3 of the output scale
+    assert err_bf <= 6e-3, (err_bf, err_fp)
+    assert err_bf < err_fp          # the BF16 input model explains most of the difference
     loss = net.loss(xg.data_ptr(), tg.data_ptr(), N, list(shape))
     ref = U.loss(pk, x.astype(np.float64), t.astype(np.float64), nd, cin, cout, base, levels)
     assert abs(loss - ref) <= 1e-4 * ref
@@ -187,6 +190,53 @@ def test_features_and_targets_match_their_numpy_definition_3d(P):
     """The same on a 3D FP64 box (x-z pure shear) coarsened by 1, 2 and 3."""
     s = E.config(3, n=(12, 10, 9), inclusion_radius=0.25, tol=1e-9)
     _lockstep(P, s, 6, (1, 2, 3))
+
+
+def test_output_scale_scales_the_output_and_its_gradient(P):
+    """With an output scale s the network's output is s times its head's, the
+    loss is taken in units of s, and the gradient is that loss's (finite
+    differences of the numpy network with its output times s)."""
+    import torch
+    nd, shape, base, levels, N = 2, (8, 8), 2, 2, 2
+    cin, cout = nd + 2, nd
+    net = P.Net(nd, cin, cout, base=base, levels=levels, seed=3)
+    table, _ = U.layer_table(nd, cin, cout, base, levels)
+    rng = np.random.default_rng(2)
+    params = net.get_params().astype(np.float64)
+    ci, co, k, wo, bo = table[-1]
+    params[wo:wo + ci * co] = rng.normal(size=ci * co) * 0.3
+    net.set_params(params.astype(np.float32))
+    pk = params.copy()
+    for (ci, co, k, wo, bo) in table:
+        pk[wo:wo + ci * co * k ** nd] = _bf16(params[wo:wo + ci * co * k ** nd])
+        pk[bo:bo + co] = params[bo:bo + co].astype(np.float32)
+    dims = tuple(reversed(shape))
+    x = rng.normal(size=(N, cin) + dims).astype(np.float32)
+    t = rng.normal(size=(N, cout) + dims).astype(np.float32)
+    xg = torch.tensor(x, device="cuda").contiguous()
+    tg = torch.tensor(t, device="cuda").contiguous()
+    y1 = torch.empty((N, cout) + dims, dtype=torch.float32, device="cuda")
+    y2 = torch.empty_like(y1)
+    net.forward(xg.data_ptr(), N, list(shape), y1.data_ptr())
+    net.set_output_scale(0.37)
+    net.forward(xg.data_ptr(), N, list(shape), y2.data_ptr())
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(y2.cpu().numpy(), 0.37 * y1.cpu().numpy(), rtol=1e-6, atol=1e-7)
+    loss, g = net.gradients(xg.data_ptr(), tg.data_ptr(), N, list(shape))
+    xr, tr = x.astype(np.float64), t.astype(np.float64)
+
+    def scaled_loss(p):      # the loss in units of the scale
+        return float(np.mean(((0.37 * U.forward(p, xr, nd, cin, cout, base, levels) - tr) / 0.37) ** 2))
+
+    assert abs(loss - scaled_loss(pk)) <= 1e-4 * loss
+    g_ref = np.zeros_like(pk)
+    for i in range(pk.size):
+        a, b = pk.copy(), pk.copy()
+        a[i] += 1e-5
+        b[i] -= 1e-5
+        g_ref[i] = (scaled_loss(a) - scaled_loss(b)) / 2e-5
+    assert np.abs(g - g_ref).max() <= 5e-3 * np.abs(g_ref).max()
+    net.close()
 
 
 def test_training_reduces_the_loss(P):
