@@ -283,6 +283,14 @@ __global__ void k_mse_final(const double *partial, long long n, double *loss) {
   if (threadIdx.x == 0) *loss = s / (double)n;
 }
 
+// Adam's denominator guard: far below any gradient the losses here produce
+// (means over millions of voxels make per-parameter gradients of 1e-9 and
+// less), so that the update stays scale-free
+#ifndef EP_ADAM_EPS
+#define EP_ADAM_EPS 1e-15f
+#endif
+constexpr float ADAM_EPS = EP_ADAM_EPS;
+
 __global__ void k_adam(float *w, __nv_bfloat16 *wb, const float *g, float *m, float *v, long long n, float lr,
                        float b1, float b2, float eps, float c1, float c2) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -958,7 +966,7 @@ ep_status ep_net_train_step(ep_net *n, const float *x, const float *t, int N, co
   u.step += 1;
   const float b1 = 0.9f, b2 = 0.999f;
   const float c1 = 1.f - powf(b1, (float)u.step), c2 = 1.f - powf(b2, (float)u.step);
-  k_adam<<<nblk(u.nparam), NT, 0, u.st>>>(u.w, u.wb, u.g, u.m, u.v, u.nparam, lr, b1, b2, 1e-8f, c1, c2);
+  k_adam<<<nblk(u.nparam), NT, 0, u.st>>>(u.w, u.wb, u.g, u.m, u.v, u.nparam, lr, b1, b2, ADAM_EPS, c1, c2);
   tc_pack(u);
   NCK(n, cudaGetLastError());
   NCK(n, cudaStreamSynchronize(u.st));
