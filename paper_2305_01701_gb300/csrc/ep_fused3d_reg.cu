@@ -14,15 +14,21 @@
 //   * z - 1 neighbours are registers carried from the previous plane;
 //   * inputs arrive through plain coalesced loads issued one plane ahead.
 // Plane t of the march computes spins at plane t, edge trials at face t and
-// plane t-1, centres t-1, edges t-1 and velocities t-2.  Four block barriers
-// separate the steps of a plane.
+// plane t-1, centres t-1, edges t-1 and velocities t-2.  Three block barriers
+// separate the steps of a plane: the input rows of plane t+1 are published
+// before the third barrier of plane t, once every read of plane t's input
+// rows lies behind the second.
 // Instruction count (the kernel is issue-bound, not bandwidth-bound):
 //   * blocks whose whole window lies inside the domain run a copy of the body
 //     in which the domain-boundary tests are compile-time true;
 //   * FP32 loads take a clamped in-box address and no test: a value read
 //     outside the box only ever enters guarded expressions;
 //   * the march is unrolled by two planes, so the shared-memory slot of each
-//     copy is a compile-time constant.
+//     copy is a compile-time constant;
+//   * offsets within an array are 32-bit when the box has fewer than 2^31
+//     points (FP32), so an address is one wide multiply-add;
+//   * the warps of the window's first and last rows, whose centres are never
+//     read, skip the centre step (rows are warp-uniform).
 #include <math.h>
 
 #include <type_traits>
@@ -67,7 +73,8 @@ struct Args {
 
 // INT: every column of the block's window lies strictly inside the domain
 // (1 <= x, y index <= n - 1), so the domain-boundary tests fold away.
-template <typename T, int H, bool INT>
+// Off: the integer type of offsets within an array.
+template <typename T, int H, bool INT, typename Off>
 __device__ __forceinline__ void reg_body(const Args<T> &A, const Geo &g, const Scal *sc, bool frozen, int kz,
                                          unsigned char *smem_raw) {
   SmemR<T, H> &S = *reinterpret_cast<SmemR<T, H> *>(smem_raw);
@@ -77,7 +84,7 @@ __device__ __forceinline__ void reg_body(const Args<T> &A, const Geo &g, const S
   const int gi = i0 - 2 + a, gj = j0 - 2 + b;
   const int kb = blockIdx.z * kz, ke = min(kb + kz, g.pz);
   const int nz = g.nz, pz = g.pz;
-  const long long px = g.px, plane = g.plane;
+  const Off px = (Off)g.px, plane = (Off)g.plane;
   const bool inb = INT || (gi >= 0 && gi < g.px && gj >= 0 && gj < g.py);
   const bool gx1 = INT || (gi >= 1 && gi <= g.nx - 1), gy1 = INT || (gj >= 1 && gj <= g.ny - 1);
   const bool gx0 = INT || (gi >= 0 && gi < g.nx), gy0 = INT || (gj >= 0 && gj < g.ny);
@@ -87,8 +94,8 @@ __device__ __forceinline__ void reg_body(const Args<T> &A, const Geo &g, const S
   // expressions); every store and the frozen-scale read are guarded by
   // in-box tests, where the clamped offset is the exact one.  FP64 keeps the
   // tested loads (fewer registers).
-  const long long col = sizeof(T) == 4 ? (long long)min(max(gj, 0), g.py - 1) * px + min(max(gi, 0), g.px - 1)
-                                       : (inb ? (long long)gj * px + gi : 0);
+  const Off col = sizeof(T) == 4 ? (Off)min(max(gj, 0), g.py - 1) * px + (Off)min(max(gi, 0), g.px - 1)
+                                 : (inb ? (Off)gj * px + (Off)gi : (Off)0);
 
   const bool out_col = a >= 2 && a < W - 2 && b >= 2 && b < H - 2;
   const T rdx = (T)g.rdx, rdy = (T)g.rdy, rdz = (T)g.rdz;
@@ -109,8 +116,8 @@ __device__ __forceinline__ void reg_body(const Args<T> &A, const Geo &g, const S
   }
 
   auto ld = [&](const T *p, int lev) -> T {
-    if constexpr (sizeof(T) == 4) return __ldg(p + (long long)min(max(lev, 0), pz - 1) * plane + col);
-    else return (inb && lev >= 0 && lev < pz) ? __ldg(p + (long long)lev * plane + col) : (T)0;
+    if constexpr (sizeof(T) == 4) return __ldg(p + ((Off)min(max(lev, 0), pz - 1) * plane + col));
+    else return (inb && lev >= 0 && lev < pz) ? __ldg(p + ((Off)lev * plane + col)) : (T)0;
   };
 
   // inputs of the next plane (loaded one plane ahead)
@@ -127,6 +134,12 @@ __device__ __forceinline__ void reg_body(const Args<T> &A, const Geo &g, const S
     n_soxy = ld(A.sos[0], c); n_tbxy = ld(A.tbs[0], c); n_sop = ld(A.sop, c); n_pb = ld(A.pb, c);
     n_yc = ld(A.yc, c);
   };
+  // the row-exchanged inputs of the prefetched plane, into its plane slot
+  auto publish = [&](const int slot) {
+    S.u0.r[rb][a] = n_u0; S.u2.r[rb][a] = n_u2; S.u1[slot].r[rb][a] = n_u1;
+    S.rq0[slot].r[rb][a] = n_rq0; S.rq1[slot].r[rb][a] = n_rq1; S.rq2.r[rb][a] = n_rq2;
+    S.rd0[slot].r[rb][a] = n_rd0; S.rd1[slot].r[rb][a] = n_rd1;
+  };
 
   // plane history (suffix: _1 plane t-1, _2 plane t-2, _3 plane t-3)
   T u0 = 0, u1 = 0, u2 = 0, u0_1 = 0, u1_1 = 0, u2_1 = 0, u0_2 = 0, u1_2 = 0, u2_2 = 0;
@@ -138,11 +151,13 @@ __device__ __forceinline__ void reg_body(const Args<T> &A, const Geo &g, const S
   T nxy_2 = 0, nxz_2 = 0, nyz_2 = 0;           // edge stress, level t-2
 
   prefetch(kb - 2);
+  publish(0);
+  __syncthreads();
   // the march unrolled by two planes: the slot parity of each copy is a
   // compile-time constant
   auto plane_step = [&](const int t, auto slc) {
     constexpr int sl = decltype(slc)::value, sl1 = sl ^ 1;  // plane slots of t and t - 1
-    // ---- 0. take this plane's inputs, publish the row-exchanged ones ----
+    // ---- 0. take this plane's inputs (their rows are already published) ----
     u0_2 = u0_1; u1_2 = u1_1; u2_2 = u2_1;
     u0_1 = u0; u1_1 = u1; u2_1 = u2;
     u0 = n_u0; u1 = n_u1; u2 = n_u2;
@@ -151,11 +166,8 @@ __device__ __forceinline__ void reg_body(const Args<T> &A, const Geo &g, const S
     const T soxz = n_soxz, soyz = n_soyz, tbxz = n_tbxz, tbyz = n_tbyz;
     const T son0 = n_son0, son1 = n_son1, son2 = n_son2, tbn0 = n_tbn0, tbn1 = n_tbn1, tbn2 = n_tbn2;
     const T soxy = n_soxy, tbxy = n_tbxy, sop = n_sop, pb = n_pb, yc = n_yc;
-    if (t + 1 < ke + 2) prefetch(t + 1);
-    S.u0.r[rb][a] = u0; S.u2.r[rb][a] = u2; S.u1[sl].r[rb][a] = u1;
-    S.rq0[sl].r[rb][a] = rq0; S.rq1[sl].r[rb][a] = rq1; S.rq2.r[rb][a] = rq2;
-    S.rd0[sl].r[rb][a] = rd0; S.rd1[sl].r[rb][a] = rd1;
-    __syncthreads();
+    const bool more = t + 1 < ke + 2;
+    if (more) prefetch(t + 1);
 
     // ---- 1. shear strain rates and spins at plane t (xy) / face t (xz, yz) ----
     T exy = 0, oxy = 0, exz = 0, oxz = 0, eyz = 0, oyz = 0;
@@ -256,7 +268,7 @@ __device__ __forceinline__ void reg_body(const Args<T> &A, const Geo &g, const S
 
     // ---- 3. pressure and return at the centres of plane t-1 ----
     T s_1 = 0, sxx_1 = 0, syy_1 = 0, szz_1 = 0;
-    {
+    if (b >= 1 && b < H - 1) {
       const T tsxy_xp = xp(tsxy), tsxy_yp = S.tsxy.r[rb + 1][a];
       const T tsxy_yp_xp = xp(tsxy_yp);
       const T tsxz_1_xp = xp(tsxz_1), tsxz_xp = xp(tsxz);
@@ -270,7 +282,7 @@ __device__ __forceinline__ void reg_body(const Args<T> &A, const Geo &g, const S
         const T tyz = qr * (tsyz_1 + tsyz_1_yp + tsyz + tsyz_yp);
         const T J2 = txy * txy + txz * txz + tyz * tyz + hf * c0v * c0v + hf * c1v * c1v + hf * c2v * c2v;
         if (frozen) {
-          s_1 = A.s[(long long)lc * plane + col];
+          s_1 = A.s[(Off)lc * plane + col];
         } else {
           T Y = Acoef * pr + yc;
           Y = Y > (T)0 ? Y : (T)0;
@@ -286,12 +298,14 @@ __device__ __forceinline__ void reg_body(const Args<T> &A, const Geo &g, const S
         const T n0 = s_1 * c0v, n1 = s_1 * c1v, n2 = s_1 * c2v;
         sxx_1 = n0 - pr; syy_1 = n1 - pr; szz_1 = n2 - pr;
         if (out_col && lc >= kb && lc < ke) {
-          const long long ec = (long long)lc * plane + col;
+          const Off ec = (Off)lc * plane + col;
           A.snn[0][ec] = n0; A.snn[1][ec] = n1; A.snn[2][ec] = n2; A.snp[ec] = pr;
         }
       }
     }
     S.s[sl1].r[rb][a] = s_1; S.syy[sl1].r[rb][a] = syy_1;
+    // every read of plane t's input rows lies behind the second barrier
+    if (more) publish(sl1);
     __syncthreads();
 
     // ---- 4. new edge deviators at level t-1 ----
@@ -308,7 +322,7 @@ __device__ __forceinline__ void reg_body(const Args<T> &A, const Geo &g, const S
       if (inner && lc >= 1 && lc <= nz - 1 && gx0 && gy1)
         nyz_1 = qr * (s_2_ym + s_2 + s_1_ym + s_1) * tsyz_1;
       if (out_col && lc >= kb && lc < ke && inb) {
-        const long long e = (long long)lc * plane + col;
+        const Off e = (Off)lc * plane + col;
         A.sns[0][e] = nxy_1; A.sns[1][e] = nxz_1; A.sns[2][e] = nyz_1;
       }
     }
@@ -321,7 +335,7 @@ __device__ __forceinline__ void reg_body(const Args<T> &A, const Geo &g, const S
       if (out_col && inb && lu >= kb && lu < ke) {
         const T nxy_2_yp = S.nxy[sl].r[rb + 1][a], syy_2_ym = S.syy[sl].r[rb - 1][a];
         const T nyz_2_yp = S.nyz[sl].r[rb + 1][a];
-        const long long e = (long long)lu * plane + col;
+        const Off e = (Off)lu * plane + col;
         T un = u0_2;
         if (gx1 && gyl && lu < nz) {
           const T R = (sxx_2 - sxx_2_xm) * rdx + (nxy_2_yp - nxy_2) * rdy + (nxz_1 - nxz_2) * rdz;
@@ -359,7 +373,7 @@ __device__ __forceinline__ void reg_body(const Args<T> &A, const Geo &g, const S
   if (t < ke + 2) plane_step(t, std::integral_constant<int, 0>{});
 }
 
-template <typename T, int H>
+template <typename T, int H, typename Off>
 __global__ void __launch_bounds__(WX *H, 1)
     k_fused3d_reg(const Args<T> A, Geo g, const Scal *sc, const DevInfo *di, int kz) {
   if (di != nullptr && *(volatile const int *)&di->done != 0) return;
@@ -367,8 +381,8 @@ __global__ void __launch_bounds__(WX *H, 1)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int i0 = blockIdx.x * OX, j0 = blockIdx.y * (H - 4);
   const bool interior = i0 - 2 >= 1 && i0 + WX - 3 <= g.nx - 1 && j0 - 2 >= 1 && j0 + H - 3 <= g.ny - 1;
-  if (interior) reg_body<T, H, true>(A, g, sc, frozen, kz, smem_raw);
-  else reg_body<T, H, false>(A, g, sc, frozen, kz, smem_raw);
+  if (interior) reg_body<T, H, true, Off>(A, g, sc, frozen, kz, smem_raw);
+  else reg_body<T, H, false, Off>(A, g, sc, frozen, kz, smem_raw);
 }
 
 template <typename T>
@@ -392,14 +406,23 @@ void launch_fused3d_reg(const Geo &g, const Stage<T> &S, const Scal *sc, const D
   A.s = S.s;
   kz = fused3d_kz(g, OX, H - 4, kz);
   dim3 grid((g.px + OX - 1) / OX, (g.py + H - 5) / (H - 4), (g.pz + kz - 1) / kz);
-  k_fused3d_reg<T, H><<<grid, WX * H, sizeof(SmemR<T, H>), st>>>(A, g, sc, di, kz);
+  if constexpr (sizeof(T) == 4) {
+    if ((long long)g.pz * g.plane < (1LL << 31)) {
+      k_fused3d_reg<T, H, int><<<grid, WX * H, sizeof(SmemR<T, H>), st>>>(A, g, sc, di, kz);
+      return;
+    }
+  }
+  k_fused3d_reg<T, H, long long><<<grid, WX * H, sizeof(SmemR<T, H>), st>>>(A, g, sc, di, kz);
 }
 
 cudaError_t fused3d_reg_configure() {
-  cudaError_t e = cudaFuncSetAttribute(k_fused3d_reg<float, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_fused3d_reg<float, 16, int>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sizeof(SmemR<float, 16>));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_fused3d_reg<double, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(k_fused3d_reg<float, 16, long long>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sizeof(SmemR<float, 16>));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_fused3d_reg<double, 8, long long>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)sizeof(SmemR<double, 8>));
 }
 
