@@ -78,7 +78,9 @@ def parse():
     ap.add_argument("--symmetry-study", action="store_true", help="the paper's large vs small increment study")
     ap.add_argument("--sym-strain", type=float, default=1.4e-3, help="total strain of the symmetry study")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-size", type=int, default=24)
+    ap.add_argument("--cpu-size", type=int, default=48, help="edge of the oracle's sample box (CPU legs)")
+    ap.add_argument("--oracle-threads", type=int, default=0,
+                    help="threads of the timed oracle: 0 every host core (OpenMP build), 1 the plain build")
     ap.add_argument("--kernel", default="auto", choices=sorted(["auto", "staged", "fused", "tma", "reg"]),
                     help="sweep kernel: auto (library default), staged, fused (cp.async), tma or reg")
     a = ap.parse_args()
@@ -152,7 +154,21 @@ class Clocks:
 
 
 # ------------------------------------------------------------ oracle arm ----
-def oracle_increment_rate(size, tol, increment, max_seconds=30.0):
+def oracle_lib(threads):
+    """The oracle build to time and the threads it uses: threads == 1 the
+    plain build; otherwise the OpenMP build (same results bit for bit) on
+    `threads` threads, 0 meaning every host core (the plain build when the
+    compiler has no OpenMP)."""
+    import oracle as O
+    if threads == 1:
+        return None, 1
+    path = O.build_omp()
+    if path is None:
+        return None, 1
+    return path, O.threads(threads if threads > 0 else (os.cpu_count() or 1), path)
+
+
+def oracle_increment_rate(size, tol, increment, max_seconds=30.0, lib_path=None):
     """Time the FP64 CPU oracle on the same setup at a small size.
 
     Runs the elastic increments untimed, then times solving `increment`
@@ -161,7 +177,7 @@ def oracle_increment_rate(size, tol, increment, max_seconds=30.0):
     import numpy as np
     import oracle as O
     s = setup_for(size, tol)
-    o = O.from_setup(s)
+    o = O.from_setup(s, lib_path=lib_path)
     rates = [s.a, 0.0, -s.a]
     for _ in range(increment - 1):
         o.apply_increment(rates, s.dt)
@@ -186,11 +202,12 @@ def oracle_increment_rate(size, tol, increment, max_seconds=30.0):
 
 
 def oracle_plan(args):
-    """The CPU baseline plan: the FP64 oracle, single-threaded as it stands,
-    timed per iteration at 64^2, 511^2, 63^3 and 127^3 (a perturbed start
-    velocity keeps it iterating; a fixed count of iterations) and over whole
-    increments at 64^2 (config 1, increments 1-12) and 63^3 (increments 1-5,
-    the last the first plastic one), with the host's core count and CPU
+    """The CPU baseline plan: the FP64 oracle, single-threaded (the plain
+    build) and on every host core (the OpenMP build, same results bit for
+    bit), timed per iteration at 64^2, 511^2, 63^3 and 127^3 (a perturbed
+    start velocity keeps it iterating; a fixed count of iterations) and over
+    whole increments at 64^2 (config 1, increments 1-12) and 63^3 (increments
+    1-5, the last the first plastic one), with the host's core count and CPU
     model.  Prints one JSON object."""
     import platform
     import numpy as np
@@ -210,11 +227,16 @@ def oracle_plan(args):
             pass
         return platform.processor() or "unknown"
 
-    res = {"host": {"nproc": os.cpu_count(), "cpu_model": cpu_model(), "machine": platform.machine(),
-                    "threads_used": 1}, "per_iteration": [], "increments": []}
-    for nd, n, iters in ((2, 64, 500), (2, 511, 60), (3, 63, 60), (3, 127, 12)):
+    res = {"host": {"nproc": os.cpu_count(), "cpu_model": cpu_model(), "machine": platform.machine()},
+           "per_iteration": [], "increments": []}
+    builds = [(None, 1)]
+    omp = oracle_lib(0)
+    if omp[0] is not None:
+        builds.append(omp)
+    for (path, thr), nd, n, iters in [(b, *c) for b in builds
+                                      for c in ((2, 64, 500), (2, 511, 60), (3, 63, 60), (3, 127, 12))]:
         s = E.config(1 if nd == 2 else 3, n=(n,) * nd, tol=1e-30)
-        o = O.from_setup(s, max_iter=iters, n_chk=iters)
+        o = O.from_setup(s, lib_path=path, max_iter=iters, n_chk=iters)
         rates = [s.a, -s.a] if nd == 2 else [s.a, 0.0, -s.a]
         o.apply_increment(rates, s.dt)
         rng = np.random.default_rng(0)
@@ -225,12 +247,13 @@ def oracle_plan(args):
         dt = time.perf_counter() - t0
         cells = n ** nd
         k = max(info["iters"], 1)
-        res["per_iteration"].append({"grid": "%d^%d" % (n, nd), "iterations": k, "ms_per_iteration": dt / k * 1e3,
+        res["per_iteration"].append({"grid": "%d^%d" % (n, nd), "threads": thr, "iterations": k,
+                                     "ms_per_iteration": dt / k * 1e3,
                                      "ns_per_cell_iteration": dt / k / cells * 1e9,
                                      "GB_per_s_algorithmic": alg_bytes_per_cell(nd, "fp64") * cells * k / dt / 1e9})
-    for nd, n, incs in ((2, 64, 12), (3, 63, 5)):
+    for (path, thr), nd, n, incs in [(b, *c) for b in builds for c in ((2, 64, 12), (3, 63, 5))]:
         s = E.config(1 if nd == 2 else 3, n=(n,) * nd, tol=1e-8 if nd == 2 else 1e-6)
-        o = O.from_setup(s)
+        o = O.from_setup(s, lib_path=path)
         rates = [s.a, -s.a] if nd == 2 else [s.a, 0.0, -s.a]
         rows = []
         for inc in range(1, incs + 1):
@@ -239,7 +262,7 @@ def oracle_plan(args):
             info = o.solve_increment()
             rows.append({"increment": inc, "iterations": info["iters"], "seconds": time.perf_counter() - t0,
                          "n_plastic": info["n_plastic"]})
-        res["increments"].append({"grid": "%d^%d" % (n, nd), "tol": s.tol, "rows": rows,
+        res["increments"].append({"grid": "%d^%d" % (n, nd), "threads": thr, "tol": s.tol, "rows": rows,
                                   "seconds_total": sum(r["seconds"] for r in rows)})
     print(json.dumps(res))
     return 0
@@ -308,12 +331,14 @@ def reference_arm(args):
     if rank != 0:
         return 0
     s = setup_for(args.size, args.tol)
+    lib_path, thr = oracle_lib(args.oracle_threads)
     # bounded sample: each step solves the timed increment on a cpu_size^3 grid
     per_inc, iters, cells = None, None, None
     times = []
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        per_inc, iters, cells = oracle_increment_rate(args.cpu_size, args.tol, args.increment, max_seconds=0.0)
+        per_inc, iters, cells = oracle_increment_rate(args.cpu_size, args.tol, args.increment, max_seconds=0.0,
+                                                      lib_path=lib_path)
         if i >= args.warmup:
             times.append(time.perf_counter() - t0)
     sec = sum(times) / len(times)
@@ -326,10 +351,10 @@ def reference_arm(args):
         "config": {"workload": "3d-ep-xz-inclusion %d^3 (oracle sample of the %d^3 workload), increment %d, tol %g"
                    % (args.cpu_size, s.n[0], args.increment, args.tol),
                    "sample_cells": cells, "iterations": iters},
-        "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                         "sample": "increment %d of the %d^3 box solved by the single-threaded FP64 oracle "
-                                   "(%d iterations, %.2f s per increment)" % (args.increment, args.cpu_size, iters,
-                                                                             per_inc)},
+        "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": thr, "kind": "oracle",
+                         "sample": "increment %d of the %d^3 box solved by the FP64 oracle on %d thread(s) "
+                                   "(%d iterations, %.2f s per increment)" % (args.increment, args.cpu_size, thr,
+                                                                             iters, per_inc)},
         "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -603,11 +628,13 @@ def our_arm(args):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        per_inc, c_iters, c_cells = oracle_increment_rate(args.cpu_size, args.tol, args.increment)
+        lib_path, thr = oracle_lib(args.oracle_threads)
+        per_inc, c_iters, c_cells = oracle_increment_rate(args.cpu_size, args.tol, args.increment, lib_path=lib_path)
         cpu = {"value": alg_bytes_per_cell(3, "fp64") * c_cells * c_iters / per_inc / 1e9, "unit": "GB/s",
-               "cores": 1, "kind": "oracle",
-               "sample": "increment %d of the same setup on a %d^3 grid, single-threaded FP64 oracle "
-                         "(%d iterations, %.2f s per increment)" % (args.increment, args.cpu_size, c_iters, per_inc)}
+               "cores": thr, "kind": "oracle",
+               "sample": "increment %d of the same setup on a %d^3 grid, FP64 oracle on %d thread(s) "
+                         "(%d iterations, %.2f s per increment)" % (args.increment, args.cpu_size, thr, c_iters,
+                                                                   per_inc)}
 
     peaks = {}
     try:

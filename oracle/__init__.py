@@ -57,6 +57,31 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+_LIB_OMP = os.path.join(_LIBDIR, "ep_oracle_omp.so")
+
+
+def build_omp(force: bool = False):
+    """The same source compiled with -fopenmp (its per-element loops then run
+    on several threads, with the same results bit for bit); returns the
+    library's path, or None where the compiler has no OpenMP."""
+    with _lock:
+        if force or not os.path.exists(_LIB_OMP) or os.path.getmtime(_LIB_OMP) < os.path.getmtime(_SRC):
+            os.makedirs(_LIBDIR, exist_ok=True)
+            tmp = _LIB_OMP + ".%d.tmp" % os.getpid()
+            cmd = ["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-D_GNU_SOURCE", "-fopenmp",
+                   "-ffp-contract=off", "-o", tmp, _SRC, "-lm"]
+            if subprocess.run(cmd, capture_output=True).returncode != 0:
+                return None
+            os.replace(tmp, _LIB_OMP)
+    return _LIB_OMP
+
+
+def threads(n: int = 0, path: str | None = None) -> int:
+    """Set (n > 0) and return the thread count of the oracle library at
+    `path` (default: the plain build, always 1)."""
+    return int(lib(path).or_threads(int(n)))
+
+
 def build_variant(source: str, tag: str) -> str:
     """Compile a modified copy of the oracle's source (a test that plants a
     mistake in the oracle to show that a pin catches it) into
@@ -117,6 +142,8 @@ def _load(path):
     L.or_pt_params.argtypes = [P, DP, DP, DP]
     L.or_set_start.argtypes = [P, DP]
     L.or_get_eval.argtypes = [P, I, DP, Lg]
+    L.or_threads.restype = I
+    L.or_threads.argtypes = [I]
     return L
 
 
@@ -267,9 +294,10 @@ def rates_for(load_plane: str, a: float, ndim: int):
     raise ValueError(load_plane)
 
 
-def from_setup(setup, **solver):
-    """An oracle grid initialised from an :class:`ep_inputs.Setup`."""
-    o = Oracle(setup.ndim, setup.n, setup.L)
+def from_setup(setup, lib_path=None, **solver):
+    """An oracle grid initialised from an :class:`ep_inputs.Setup` (on the
+    library at lib_path, default the plain build)."""
+    o = Oracle(setup.ndim, setup.n, setup.L, lib_path=lib_path)
     o.set_material(setup.K, setup.G, setup.mu_s, setup.phi_deg, setup.psi_deg, setup.cohesion())
     kw = dict(tol=setup.tol)
     kw.update(solver)

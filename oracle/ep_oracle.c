@@ -55,11 +55,19 @@
  *    each in stress units and relative to max|sigma|, every n_chk iterations;
  *    each residual is the pseudo-time rate of its state (velocity, deviator,
  *    pressure) averaged over the check interval.
+ *
+ * Threads: the loops of one iteration that write one element per loop index
+ * carry OpenMP pragmas; norms and reductions stay serial.  Each element's
+ * arithmetic is the same on any thread, so a build with -fopenmp gives the
+ * same bits as the plain build (the default, which ignores the pragmas).
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* ---- status codes and field ids (same numbering as the library's API) ---- */
 enum { OR_OK = 0, OR_ERR_ARG = 1, OR_ERR_OOM = 3, OR_ERR_STATE = 4,
@@ -297,6 +305,7 @@ static void strain_rates(or_grid *g, double *const vv[3]) {
   const int nx = g->nx, ny = g->ny, nz = g->nz;
   const double dx = g->dx, dy = g->dy, dz = g->dz;
   double *vx = vv[0], *vy = vv[1], *vz = vv[2];
+  #pragma omp parallel for collapse(2) schedule(static)
   for (int k = 0; k < nz; ++k) for (int j = 0; j < ny; ++j) for (int i = 0; i < nx; ++i) {
     long c = CI(i, j, k);
     g->en[0][c] = (vx[FXI(i + 1, j, k)] - vx[FXI(i, j, k)]) / dx;
@@ -308,6 +317,7 @@ static void strain_rates(or_grid *g, double *const vv[3]) {
     }
   }
   /* xy: 2D vertices or 3D xy-edges; walls carry zero */
+  #pragma omp parallel for collapse(2) schedule(static)
   for (int k = 0; k < nz; ++k) for (int j = 0; j <= ny; ++j) for (int i = 0; i <= nx; ++i) {
     long e = XYI(i, j, k);
     if (i == 0 || i == nx || j == 0 || j == ny) { g->es[0][e] = 0.0; g->om[0][e] = 0.0; continue; }
@@ -317,6 +327,7 @@ static void strain_rates(or_grid *g, double *const vv[3]) {
     g->om[0][e] = 0.5 * (a - b);
   }
   if (g->ndim == 2) return;
+  #pragma omp parallel for collapse(2) schedule(static)
   for (int k = 0; k <= nz; ++k) for (int j = 0; j < ny; ++j) for (int i = 0; i <= nx; ++i) {
     long e = XZI(i, j, k);
     if (i == 0 || i == nx || k == 0 || k == nz) { g->es[1][e] = 0.0; g->om[1][e] = 0.0; continue; }
@@ -325,6 +336,7 @@ static void strain_rates(or_grid *g, double *const vv[3]) {
     g->es[1][e] = 0.5 * (a + b);
     g->om[1][e] = 0.5 * (a - b);
   }
+  #pragma omp parallel for collapse(2) schedule(static)
   for (int k = 0; k <= nz; ++k) for (int j = 0; j <= ny; ++j) for (int i = 0; i < nx; ++i) {
     long e = YZI(i, j, k);
     if (j == 0 || j == ny || k == 0 || k == nz) { g->es[2][e] = 0.0; g->om[2][e] = 0.0; continue; }
@@ -342,6 +354,7 @@ static void rotated_history_2d(or_grid *g) {
   const int nx = g->nx, ny = g->ny;
   const double dt = g->dt;
   double *txy = g->ts[0], *wxy = g->om[0];
+  #pragma omp parallel for schedule(static)
   for (int j = 0; j < ny; ++j) for (int i = 0; i < nx; ++i) {
     long c = CI(i, j, 0);
     double q = 0.0;
@@ -351,6 +364,7 @@ static void rotated_history_2d(or_grid *g) {
     g->tJn[0][c] = g->tn[0][c] + dt * (2.0 * q);    /* R_xx =  2 t_xy w_xy */
     g->tJn[1][c] = g->tn[1][c] + dt * (-2.0 * q);   /* R_yy = -2 t_xy w_xy */
   }
+  #pragma omp parallel for schedule(static)
   for (int j = 0; j <= ny; ++j) for (int i = 0; i <= nx; ++i) {
     long e = XYI(i, j, 0);
     if (i == 0 || i == nx || j == 0 || j == ny) { g->tJs[0][e] = 0.0; continue; }
@@ -371,6 +385,7 @@ static void rotated_history_3d(or_grid *g) {
   const double dt = g->dt;
   double *txy = g->ts[0], *txz = g->ts[1], *tyz = g->ts[2];
   double *wxy = g->om[0], *wxz = g->om[1], *wyz = g->om[2];
+  #pragma omp parallel for collapse(2) schedule(static)
   for (int k = 0; k < nz; ++k) for (int j = 0; j < ny; ++j) for (int i = 0; i < nx; ++i) {
     long c = CI(i, j, k);
     double pxy = 0.0, pxz = 0.0, pyz = 0.0;
@@ -386,6 +401,7 @@ static void rotated_history_3d(or_grid *g) {
     g->tJn[1][c] = g->tn[1][c] + dt * (-2.0 * (pxy - pyz));     /* R_yy */
     g->tJn[2][c] = g->tn[2][c] + dt * (-2.0 * (pxz + pyz));     /* R_zz */
   }
+  #pragma omp parallel for collapse(2) schedule(static)
   for (int k = 0; k < nz; ++k) for (int j = 0; j <= ny; ++j) for (int i = 0; i <= nx; ++i) {
     long e = XYI(i, j, k);
     if (i == 0 || i == nx || j == 0 || j == ny) { g->tJs[0][e] = 0.0; continue; }
@@ -403,6 +419,7 @@ static void rotated_history_3d(or_grid *g) {
     }
     g->tJs[0][e] = txy[e] + dt * r;
   }
+  #pragma omp parallel for collapse(2) schedule(static)
   for (int k = 0; k <= nz; ++k) for (int j = 0; j < ny; ++j) for (int i = 0; i <= nx; ++i) {
     long e = XZI(i, j, k);
     if (i == 0 || i == nx || k == 0 || k == nz) { g->tJs[1][e] = 0.0; continue; }
@@ -420,6 +437,7 @@ static void rotated_history_3d(or_grid *g) {
     }
     g->tJs[1][e] = txz[e] + dt * r;
   }
+  #pragma omp parallel for collapse(2) schedule(static)
   for (int k = 0; k <= nz; ++k) for (int j = 0; j <= ny; ++j) for (int i = 0; i < nx; ++i) {
     long e = YZI(i, j, k);
     if (j == 0 || j == ny || k == 0 || k == nz) { g->tJs[2][e] = 0.0; continue; }
@@ -446,6 +464,7 @@ static void rotated_history_3d(or_grid *g) {
 /* ------------------------------------------------------------------------ */
 static void trial(or_grid *g) {
   long nc = n_centres(g);
+  #pragma omp parallel for schedule(static)
   for (long c = 0; c < nc; ++c) {
     const double G = G_centre(g, c), eta = eta_for(g, G), c2 = eta / (G * g->dt);
     for (int d = 0; d < g->ndim; ++d)
@@ -453,6 +472,7 @@ static void trial(or_grid *g) {
   }
   for (int s = 0; s < n_shear_comp(g); ++s) {
     int ex, ey, ez; shear_dims(g, s, &ex, &ey, &ez);
+    #pragma omp parallel for collapse(2) schedule(static)
     for (int k = 0; k < ez; ++k) for (int j = 0; j < ey; ++j) for (int i = 0; i < ex; ++i) {
       const long e = ((long)k * ey + j) * ex + i;
       const double G = G_shear(g, s, i, j, k), eta = eta_for(g, G), c2 = eta / (G * g->dt);
@@ -502,11 +522,13 @@ static void pt_stress(or_grid *g, double bt, double bp) {
   long nc = n_centres(g);
   if (!g->incompressible) {
     /* pressure, Eq. A2ssP: p = bp p_k + (1 - bp) (p_hat - K dt div v) */
+    #pragma omp parallel for schedule(static)
     for (long c = 0; c < nc; ++c)
       g->pc[c] = bp * g->p_k[c] + (1.0 - bp) * (g->p[c] - g->K * g->dt * g->div[c]);
   } else if (bt != 0.0 || bp != 0.0) {
     /* pressure, Eq. A2ssP2 with pseudo step 1: p = p_k - K~ div v */
     const double Kt = pt_params(g).Kt;
+    #pragma omp parallel for schedule(static)
     for (long c = 0; c < nc; ++c) g->pc[c] = g->p_k[c] - Kt * g->div[c];
   } else {
     /* the physical response: the pressure is no function of v here, it
@@ -514,13 +536,16 @@ static void pt_stress(or_grid *g, double bt, double bp) {
     memcpy(g->pc, g->p, sizeof(double) * nc);
   }
   /* relaxed trial deviator, Eq. A23ssP: T = bt tau_k + (1 - bt) tau_tr */
+  #pragma omp parallel for schedule(static)
   for (long c = 0; c < nc; ++c)
     for (int d = 0; d < g->ndim; ++d) g->Tn[d][c] = bt * g->tn_k[d][c] + (1.0 - bt) * g->trn[d][c];
   for (int s = 0; s < n_shear_comp(g); ++s) {
     long ns = n_shear(g, s);
+    #pragma omp parallel for schedule(static)
     for (long e = 0; e < ns; ++e) g->Ts[s][e] = bt * g->ts_k[s][e] + (1.0 - bt) * g->trs[s][e];
   }
   /* Drucker-Prager return at centres (Eqs. A61, A611, A6121lambda) */
+  #pragma omp parallel for collapse(2) schedule(static)
   for (int k = 0; k < nz; ++k) for (int j = 0; j < ny; ++j) for (int i = 0; i < nx; ++i) {
     long c = CI(i, j, k);
     double Txy = 0.25 * (g->Ts[0][XYI(i, j, k)] + g->Ts[0][XYI(i + 1, j, k)] +
@@ -541,6 +566,7 @@ static void pt_stress(or_grid *g, double bt, double bp) {
     for (int d = 0; d < g->ndim; ++d) g->sn[d][c] = g->s[c] * g->Tn[d][c];
   }
   /* vertices / edges: arithmetic mean of the adjacent centre scales */
+  #pragma omp parallel for collapse(2) schedule(static)
   for (int k = 0; k < nz; ++k) for (int j = 0; j <= ny; ++j) for (int i = 0; i <= nx; ++i) {
     long e = XYI(i, j, k);
     if (i == 0 || i == nx || j == 0 || j == ny) { g->ss[0][e] = 0.0; continue; }
@@ -548,12 +574,14 @@ static void pt_stress(or_grid *g, double bt, double bp) {
     g->ss[0][e] = sb * g->Ts[0][e];
   }
   if (g->ndim == 2) return;
+  #pragma omp parallel for collapse(2) schedule(static)
   for (int k = 0; k <= nz; ++k) for (int j = 0; j < ny; ++j) for (int i = 0; i <= nx; ++i) {
     long e = XZI(i, j, k);
     if (i == 0 || i == nx || k == 0 || k == nz) { g->ss[1][e] = 0.0; continue; }
     double sb = 0.25 * (g->s[CI(i - 1, j, k - 1)] + g->s[CI(i, j, k - 1)] + g->s[CI(i - 1, j, k)] + g->s[CI(i, j, k)]);
     g->ss[1][e] = sb * g->Ts[1][e];
   }
+  #pragma omp parallel for collapse(2) schedule(static)
   for (int k = 0; k <= nz; ++k) for (int j = 0; j <= ny; ++j) for (int i = 0; i < nx; ++i) {
     long e = YZI(i, j, k);
     if (j == 0 || j == ny || k == 0 || k == nz) { g->ss[2][e] = 0.0; continue; }
@@ -570,6 +598,7 @@ static void residual(or_grid *g) {
   const double dx = g->dx, dy = g->dy, dz = g->dz;
   double *sxy = g->ss[0], *sxz = g->ss[1], *syz = g->ss[2];
   const int d3 = g->ndim == 3;
+  #pragma omp parallel for collapse(2) schedule(static)
   for (int k = 0; k < nz; ++k) for (int j = 0; j < ny; ++j) for (int i = 0; i <= nx; ++i) {
     long fi = FXI(i, j, k);
     if (i == 0 || i == nx) { g->R[0][fi] = 0.0; continue; }
@@ -578,6 +607,7 @@ static void residual(or_grid *g) {
     if (d3) r += (sxz[XZI(i, j, k + 1)] - sxz[XZI(i, j, k)]) / dz;
     g->R[0][fi] = r + g->f[0][fi];
   }
+  #pragma omp parallel for collapse(2) schedule(static)
   for (int k = 0; k < nz; ++k) for (int j = 0; j <= ny; ++j) for (int i = 0; i < nx; ++i) {
     long fi = FYI(i, j, k);
     if (j == 0 || j == ny) { g->R[1][fi] = 0.0; continue; }
@@ -587,6 +617,7 @@ static void residual(or_grid *g) {
     g->R[1][fi] = r + g->f[1][fi];
   }
   if (!d3) return;
+  #pragma omp parallel for collapse(2) schedule(static)
   for (int k = 0; k <= nz; ++k) for (int j = 0; j < ny; ++j) for (int i = 0; i < nx; ++i) {
     long fi = FZI(i, j, k);
     if (k == 0 || k == nz) { g->R[2][fi] = 0.0; continue; }
@@ -954,6 +985,7 @@ int or_solve_increment(or_grid *g, or_info *info) {
     accept_stress(g);
     for (int d = 0; d < g->ndim; ++d) {
       int ex, ey, ez; face_dims(g, d, &ex, &ey, &ez);
+#pragma omp parallel for collapse(2) schedule(static)
       for (int kk = 0; kk < ez; ++kk) for (int j = 0; j < ey; ++j) for (int i = 0; i < ex; ++i) {
         if (is_boundary_face(g, d, i, j, kk)) continue;
         long id = ((long)kk * ey + j) * ex + i;
@@ -970,6 +1002,18 @@ int or_solve_increment(or_grid *g, or_info *info) {
 /* Evaluate at a caller-given face velocity (concatenated x, y[, z], walls
  * included) with the physical response (no pseudo-time memory): the stress
  * and residual of the fixed point at v.  Returns max|R| and max|sigma|. */
+/* Threads of the per-iteration loops: n > 0 sets their number; returns the
+ * number in use (1 in a build without OpenMP). */
+int or_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
+
 int or_eval(or_grid *g, const double *v, double *max_r, double *max_sig) {
   if (!g->in_increment) return OR_ERR_STATE;
   long off = 0;
