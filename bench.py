@@ -407,12 +407,9 @@ def aggregate(torch, dist, seconds, units, device):
 # dominant kernel from one ncu capture of the benchmark command, by kernel and
 # box size; the entry must be dropped when the kernel changes.
 # DRAM bytes per launch of the dominant kernel from an ncu capture of its
-# current build (profiles/k_fused3d_reg_127cube.md)
-NCU_TRAFFIC = {("k_fused3d_reg", 127): 271.7e6,
-               ("k_fused3d_reg", 511): 271.7e6 * 133432831 / 2048383}
-NCU_SOURCE = {("k_fused3d_reg", 127): "ncu --set full capture of one launch at 127^3 (profiles/)",
-              ("k_fused3d_reg", 511): "ncu --set full capture of one launch at 127^3 (profiles/), the per-cell "
-                                      "traffic scaled to 511^3 by the cell count"}
+# current build (filled from profiles/ once captured; null until then)
+NCU_TRAFFIC = {}
+NCU_SOURCE = {}
 # FP64 flops per cell of one staged FP64 sweep (dadd + dmul + 2 dfma thread
 # instructions of its five kernels, counted by ncu at 127^3; profiles/)
 FP64_FLOPS_PER_CELL = 322.5

@@ -28,7 +28,8 @@
 //   * offsets within an array are 32-bit when the box has fewer than 2^31
 //     points (FP32), so an address is one wide multiply-add;
 //   * the warps of the window's first and last rows, whose centres are never
-//     read, skip the centre step (rows are warp-uniform).
+//     read, skip the centre step, and the first row's warp skips the xz-edge
+//     and centre trials (rows are warp-uniform).
 #include <math.h>
 
 #include <type_traits>
@@ -216,7 +217,7 @@ __device__ __forceinline__ void reg_body(const Args<T> &A, const Geo &g, const S
       const T pxz_1_xp = xp(pxz_1), pxz_xp = xp(pxz);
       const T pyz_1_yp = S.pyz[sl1].r[rb + 1][a], pyz_yp = S.pyz[sl].r[rb + 1][a];
 
-      if (b < H - 1 && t >= 1 && t <= nz - 1)
+      if (b >= 1 && b < H - 1 && t >= 1 && t <= nz - 1)
       if (a >= 1 && gx1 && gy0) {
         const T dzx = qr * (rd1_1_xm + rd1_1 + rd1_xm + rd1);
         const T Tyz = qr * (rq2_xm + rq2 + rq2_yp_xm + rq2_yp);
@@ -246,7 +247,7 @@ __device__ __forceinline__ void reg_body(const Args<T> &A, const Geo &g, const S
         const T tr = tbxy + two_eta * exy_1 + (oxy_1 * dyx + Tyz * Wxz + Txz * Wyz);
         tsxy = bt * soxy + ob * tr;
       }
-      if (b < H - 1 && lc >= 0 && lc < nz)
+      if (b >= 1 && b < H - 1 && lc >= 0 && lc < nz)
       if (a < W - 1 && gx0 && gy0) {
         exx = (u0_1_xp - u0_1) * rdx;
         eyy = (u1_1_yp - u1_1) * rdy;
