@@ -528,13 +528,21 @@ bool use_fused(const ep_grid *h) {
   return v == EP_KERNEL_FUSED || v == EP_KERNEL_FUSED_TMA || v == EP_KERNEL_FUSED_REG;
 }
 
+// the check iteration runs fused too: the FP32 register sweep reduces the
+// stopping measures itself (the other flavours and FP64 take the staged
+// check iteration)
+template <typename T>
+bool fused_check(const ep_grid *h) {
+  return sizeof(T) == 4 && use_fused<T>(h) && fused_variant(h) == EP_KERNEL_FUSED_REG;
+}
+
 // one fused 3D iteration in the grid's chosen flavour
 template <typename T>
-bool launch_fused_any(const ep_grid *h, const Stage<T> &S, const DevInfo *di, cudaStream_t st) {
+bool launch_fused_any(const ep_grid *h, const Stage<T> &S, DevInfo *di, cudaStream_t st, bool check = false) {
   const int v = fused_variant(h);
   if (v == EP_KERNEL_FUSED_TMA) return launch_fused3d_tma<T>(h->g, S, h->dscal, di, h->kz, st);
   if (v == EP_KERNEL_FUSED_REG) {
-    launch_fused3d_reg<T>(h->g, S, h->dscal, di, h->kz, st);
+    launch_fused3d_reg<T>(h->g, S, h->dscal, di, h->kz, st, check);
     return true;
   }
   launch_fused3d<T>(h->g, S, h->dscal, di, h->kz, st);
@@ -564,13 +572,14 @@ ep_status capture_chunk(ep_grid *h) {
   for (int it = 0; !f2 && it < h->opts.n_chk; ++it) {
     Stage<T> S = sweep_stage<T>(h, it & 1);
     const int chk = it == 0;
-    if (!chk && use_fused<T>(h)) {
-      if (!launch_fused_any<T>(h, S, h->dinfo, h->cap)) {
+    if ((!chk || fused_check<T>(h)) && use_fused<T>(h)) {
+      if (!launch_fused_any<T>(h, S, h->dinfo, h->cap, chk)) {
         cudaGraph_t gr;
         cudaStreamEndCapture(h->cap, &gr);
         if (gr) cudaGraphDestroy(gr);
         return fail(h, EP_ERR_CUDA, "tensor map encoding failed");
       }
+      if (chk) launch_check(h->dinfo, h->dscal, h->cap);
       continue;
     }
     launch_strain<T>(g, S, h->dscal, h->dinfo, h->cap);

@@ -30,6 +30,12 @@
 //   * the warps of the window's first and last rows, whose centres are never
 //     read, skip the centre step, and the first row's warp skips the xz-edge
 //     and centre trials (rows are warp-uniform).
+// Check iterations (FP32, CHK = true) also reduce the stopping measures of
+// Eqs. Convergence1-3 over the points each block writes, the same point sets
+// and the same snapshot updates as the staged check iteration: max|sigma|,
+// max|tau - tau_chk|, max|p - p_chk| at centres and edges, max|R|,
+// max|u - u_chk| and max|v0 + u| at faces, and they store the centre scales
+// (held when plasticity freezes).  One atomic per block and measure.
 #include <math.h>
 
 #include <type_traits>
@@ -69,15 +75,45 @@ struct Args {
   const T *u[3], *rq[3], *rd[2];
   const T *son[3], *sos[3], *sop, *tbn[3], *tbs[3], *pb, *yc;
   T *snn[3], *sns[3], *snp, *uo[3];
-  const T *s;   // centre return scales (read when plasticity is frozen)
+  T *s;   // centre return scales (read when plasticity is frozen, written by checks)
+  T *cn[3], *cs[3], *cp, *uchk[3];   // state at the previous check (check iterations)
+  const double *v0[3];               // start velocity (check iterations)
 };
+
+template <typename T>
+__device__ __forceinline__ T maxt(T a, T b) { return (a > b || a != a) ? a : b; }
+
+// block-wide max of a non-negative value as its IEEE bits (integer order; a
+// NaN sorts above infinity), one atomic per block
+__device__ __forceinline__ void block_max_bits(double v, unsigned long long *slot) {
+  __shared__ unsigned long long part[32];
+  unsigned long long b = (unsigned long long)__double_as_longlong(fabs(v));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(FULL, b, o);
+    b = b > w ? b : w;
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) part[wid] = b;
+  __syncthreads();
+  if (wid == 0) {
+    b = lane < (int)(blockDim.x >> 5) ? part[lane] : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long w = __shfl_xor_sync(FULL, b, o);
+      b = b > w ? b : w;
+    }
+    if (lane == 0 && b) atomicMax(slot, b);
+  }
+}
 
 // INT: every column of the block's window lies strictly inside the domain
 // (1 <= x, y index <= n - 1), so the domain-boundary tests fold away.
-// Off: the integer type of offsets within an array.
-template <typename T, int H, bool INT, typename Off>
-__device__ __forceinline__ void reg_body(const Args<T> &A, const Geo &g, const Scal *sc, bool frozen, int kz,
-                                         unsigned char *smem_raw) {
+// Off: the integer type of offsets within an array.  CHK: a check iteration.
+template <typename T, int H, bool INT, typename Off, bool CHK>
+__device__ __forceinline__ void reg_body(const Args<T> &A, const Geo &g, const Scal *sc, DevInfo *di, bool frozen,
+                                         int kz, unsigned char *smem_raw) {
   SmemR<T, H> &S = *reinterpret_cast<SmemR<T, H> *>(smem_raw);
   constexpr int W = WX;
   const int a = threadIdx.x & 31, b = threadIdx.x >> 5;
@@ -150,6 +186,9 @@ __device__ __forceinline__ void reg_body(const Args<T> &A, const Geo &g, const S
   T s_2 = 0;                                   // centre scale, plane t-2
   T sxx_2 = 0, syy_2 = 0, szz_2 = 0, szz_3 = 0;  // centre stress minus pressure
   T nxy_2 = 0, nxz_2 = 0, nyz_2 = 0;           // edge stress, level t-2
+  // check iterations: the stopping measures over this block's points
+  T c_sig = 0, c_dtau = 0, c_dp = 0, c_r = 0, c_du = 0;
+  double c_vm = 0.0;
 
   prefetch(kb - 2);
   publish(0);
@@ -301,6 +340,15 @@ __device__ __forceinline__ void reg_body(const Args<T> &A, const Geo &g, const S
         if (out_col && lc >= kb && lc < ke) {
           const Off ec = (Off)lc * plane + col;
           A.snn[0][ec] = n0; A.snn[1][ec] = n1; A.snn[2][ec] = n2; A.snp[ec] = pr;
+          if constexpr (CHK) {   // a centre of the box (lc < nz, gi < nx, gj < ny hold here)
+            if (!frozen) A.s[ec] = s_1;
+            c_sig = maxt(c_sig, maxt((T)fabs(n0 - pr), maxt((T)fabs(n1 - pr), (T)fabs(n2 - pr))));
+            c_dtau = maxt(c_dtau, maxt((T)fabs(n0 - A.cn[0][ec]),
+                                       maxt((T)fabs(n1 - A.cn[1][ec]), (T)fabs(n2 - A.cn[2][ec]))));
+            c_dp = maxt(c_dp, (T)fabs(pr - A.cp[ec]));
+            A.cn[0][ec] = n0; A.cn[1][ec] = n1; A.cn[2][ec] = n2; A.cp[ec] = pr;
+            if (isnan(s_1) || isnan(pr)) c_sig = (T)NAN;
+          }
         }
       }
     }
@@ -325,6 +373,14 @@ __device__ __forceinline__ void reg_body(const Args<T> &A, const Geo &g, const S
       if (out_col && lc >= kb && lc < ke && inb) {
         const Off e = (Off)lc * plane + col;
         A.sns[0][e] = nxy_1; A.sns[1][e] = nxz_1; A.sns[2][e] = nyz_1;
+        if constexpr (CHK) {
+          if (gi <= g.nx && gj <= g.ny && lc <= nz) {   // the staged check's edge points
+            c_sig = maxt(c_sig, maxt((T)fabs(nxy_1), maxt((T)fabs(nxz_1), (T)fabs(nyz_1))));
+            c_dtau = maxt(c_dtau, maxt((T)fabs(nxy_1 - A.cs[0][e]),
+                                       maxt((T)fabs(nxz_1 - A.cs[1][e]), (T)fabs(nyz_1 - A.cs[2][e]))));
+            A.cs[0][e] = nxy_1; A.cs[1][e] = nxz_1; A.cs[2][e] = nyz_1;
+          }
+        }
       }
     }
     S.nxy[sl1].r[rb][a] = nxy_1; S.nyz[sl1].r[rb][a] = nyz_1;
@@ -341,20 +397,44 @@ __device__ __forceinline__ void reg_body(const Args<T> &A, const Geo &g, const S
         if (gx1 && gyl && lu < nz) {
           const T R = (sxx_2 - sxx_2_xm) * rdx + (nxy_2_yp - nxy_2) * rdy + (nxz_1 - nxz_2) * rdz;
           un = u0_2 + vs * R;
+          if constexpr (CHK) c_r = maxt(c_r, (T)fabs(R));
         }
         A.uo[0][e] = un;
+        if constexpr (CHK) {
+          if (gi <= g.nx && gj < g.ny && lu < nz) {   // x-faces
+            c_du = maxt(c_du, (T)fabs(un - A.uchk[0][e]));
+            c_vm = maxt(c_vm, fabs(A.v0[0][e] + (double)u0_2));
+            A.uchk[0][e] = un;
+          }
+        }
         un = u1_2;
         if (gy1 && gxl && lu < nz) {
           const T R = (syy_2 - syy_2_ym) * rdy + (nxy_2_xp - nxy_2) * rdx + (nyz_1 - nyz_2) * rdz;
           un = u1_2 + vs * R;
+          if constexpr (CHK) c_r = maxt(c_r, (T)fabs(R));
         }
         A.uo[1][e] = un;
+        if constexpr (CHK) {
+          if (gi < g.nx && gj <= g.ny && lu < nz) {   // y-faces
+            c_du = maxt(c_du, (T)fabs(un - A.uchk[1][e]));
+            c_vm = maxt(c_vm, fabs(A.v0[1][e] + (double)u1_2));
+            A.uchk[1][e] = un;
+          }
+        }
         un = u2_2;
         if (lu >= 1 && lu <= nz - 1 && gxl && gyl) {
           const T R = (szz_2 - szz_3) * rdz + (nxz_2_xp - nxz_2) * rdx + (nyz_2_yp - nyz_2) * rdy;
           un = u2_2 + vs * R;
+          if constexpr (CHK) c_r = maxt(c_r, (T)fabs(R));
         }
         A.uo[2][e] = un;
+        if constexpr (CHK) {
+          if (gi < g.nx && gj < g.ny && lu <= nz) {   // z-faces
+            c_du = maxt(c_du, (T)fabs(un - A.uchk[2][e]));
+            c_vm = maxt(c_vm, fabs(A.v0[2][e] + (double)u2_2));
+            A.uchk[2][e] = un;
+          }
+        }
       }
     }
 
@@ -372,18 +452,26 @@ __device__ __forceinline__ void reg_body(const Args<T> &A, const Geo &g, const S
     plane_step(t + 1, std::integral_constant<int, 1>{});
   }
   if (t < ke + 2) plane_step(t, std::integral_constant<int, 0>{});
+  if constexpr (CHK) {
+    block_max_bits((double)c_sig, &di->red[RED_SIG]);
+    block_max_bits((double)c_dtau, &di->red[RED_DTAU]);
+    block_max_bits((double)c_dp, &di->red[RED_DP]);
+    block_max_bits((double)c_r, &di->red[RED_R]);
+    block_max_bits((double)c_du, &di->red[RED_DU]);
+    block_max_bits(c_vm, &di->red[RED_V]);
+  }
 }
 
-template <typename T, int H, typename Off>
+template <typename T, int H, typename Off, bool CHK>
 __global__ void __launch_bounds__(WX *H, 1)
-    k_fused3d_reg(const Args<T> A, Geo g, const Scal *sc, const DevInfo *di, int kz) {
+    k_fused3d_reg(const Args<T> A, Geo g, const Scal *sc, DevInfo *di, int kz) {
   if (di != nullptr && *(volatile const int *)&di->done != 0) return;
   const bool frozen = di != nullptr && di->frozen;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int i0 = blockIdx.x * OX, j0 = blockIdx.y * (H - 4);
   const bool interior = i0 - 2 >= 1 && i0 + WX - 3 <= g.nx - 1 && j0 - 2 >= 1 && j0 + H - 3 <= g.ny - 1;
-  if (interior) reg_body<T, H, true, Off>(A, g, sc, frozen, kz, smem_raw);
-  else reg_body<T, H, false, Off>(A, g, sc, frozen, kz, smem_raw);
+  if (interior) reg_body<T, H, true, Off, CHK>(A, g, sc, di, frozen, kz, smem_raw);
+  else reg_body<T, H, false, Off, CHK>(A, g, sc, di, frozen, kz, smem_raw);
 }
 
 template <typename T>
@@ -392,44 +480,59 @@ constexpr int reg_rows() { return sizeof(T) == 4 ? 16 : 8; }
 }  // namespace
 
 // One fused iteration, register z-march flavour: reads buffer b of the
-// stage, writes 1 - b.
+// stage, writes 1 - b.  check (FP32 only): a check iteration, which also
+// reduces the stopping measures into di and updates the check snapshots.
 template <typename T>
-void launch_fused3d_reg(const Geo &g, const Stage<T> &S, const Scal *sc, const DevInfo *di, int kz, cudaStream_t st) {
+void launch_fused3d_reg(const Geo &g, const Stage<T> &S, const Scal *sc, DevInfo *di, int kz, cudaStream_t st,
+                        bool check) {
   constexpr int H = reg_rows<T>();
   Args<T> A;
   for (int d = 0; d < 3; ++d) {
     A.u[d] = S.u[d]; A.rq[d] = S.rq[d]; A.son[d] = S.son[d]; A.sos[d] = S.sos[d];
     A.tbn[d] = S.tbn[d]; A.tbs[d] = S.tbs[d];
     A.snn[d] = S.snn[d]; A.sns[d] = S.sns[d]; A.uo[d] = S.uo[d];
+    A.cn[d] = S.cn[d]; A.cs[d] = S.cs[d]; A.uchk[d] = S.uchk[d]; A.v0[d] = S.v0[d];
   }
   A.rd[0] = S.rd[0]; A.rd[1] = S.rd[1];
   A.sop = S.sop; A.pb = S.pb; A.yc = S.yc; A.snp = S.snp;
-  A.s = S.s;
+  A.s = S.s; A.cp = S.cp;
   kz = fused3d_kz(g, OX, H - 4, kz);
   dim3 grid((g.px + OX - 1) / OX, (g.py + H - 5) / (H - 4), (g.pz + kz - 1) / kz);
+  const size_t sm = sizeof(SmemR<T, H>);
   if constexpr (sizeof(T) == 4) {
-    if ((long long)g.pz * g.plane < (1LL << 31)) {
-      k_fused3d_reg<T, H, int><<<grid, WX * H, sizeof(SmemR<T, H>), st>>>(A, g, sc, di, kz);
-      return;
+    const bool o32 = (long long)g.pz * g.plane < (1LL << 31);
+    if (check) {
+      if (o32) k_fused3d_reg<T, H, int, true><<<grid, WX * H, sm, st>>>(A, g, sc, di, kz);
+      else k_fused3d_reg<T, H, long long, true><<<grid, WX * H, sm, st>>>(A, g, sc, di, kz);
+    } else {
+      if (o32) k_fused3d_reg<T, H, int, false><<<grid, WX * H, sm, st>>>(A, g, sc, di, kz);
+      else k_fused3d_reg<T, H, long long, false><<<grid, WX * H, sm, st>>>(A, g, sc, di, kz);
     }
+  } else {
+    k_fused3d_reg<T, H, long long, false><<<grid, WX * H, sm, st>>>(A, g, sc, di, kz);
   }
-  k_fused3d_reg<T, H, long long><<<grid, WX * H, sizeof(SmemR<T, H>), st>>>(A, g, sc, di, kz);
 }
 
 cudaError_t fused3d_reg_configure() {
-  cudaError_t e = cudaFuncSetAttribute(k_fused3d_reg<float, 16, int>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sizeof(SmemR<float, 16>));
+  const int sf = (int)sizeof(SmemR<float, 16>);
+  cudaError_t e = cudaFuncSetAttribute(k_fused3d_reg<float, 16, int, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, sf);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_fused3d_reg<float, 16, long long, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             sf);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_fused3d_reg<float, 16, int, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sf);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_fused3d_reg<float, 16, long long, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             sf);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_fused3d_reg<float, 16, long long>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)sizeof(SmemR<float, 16>));
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_fused3d_reg<double, 8, long long>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(k_fused3d_reg<double, 8, long long, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)sizeof(SmemR<double, 8>));
 }
 
-template void launch_fused3d_reg<float>(const Geo &, const Stage<float> &, const Scal *, const DevInfo *, int,
-                                        cudaStream_t);
-template void launch_fused3d_reg<double>(const Geo &, const Stage<double> &, const Scal *, const DevInfo *, int,
-                                         cudaStream_t);
+template void launch_fused3d_reg<float>(const Geo &, const Stage<float> &, const Scal *, DevInfo *, int, cudaStream_t,
+                                        bool);
+template void launch_fused3d_reg<double>(const Geo &, const Stage<double> &, const Scal *, DevInfo *, int,
+                                         cudaStream_t, bool);
 
 }  // namespace ep

@@ -221,7 +221,8 @@ bool launch_fused3d_tma(const Geo &g, const Stage<T> &S, const Scal *sc, const D
 cudaError_t fused3d_tma_configure();
 // register z-march variant (ep_fused3d_reg.cu)
 template <typename T>
-void launch_fused3d_reg(const Geo &g, const Stage<T> &S, const Scal *sc, const DevInfo *di, int kz, cudaStream_t st);
+void launch_fused3d_reg(const Geo &g, const Stage<T> &S, const Scal *sc, DevInfo *di, int kz, cudaStream_t st,
+                        bool check = false);
 cudaError_t fused3d_reg_configure();
 
 // ---- increment set-up and commit (FP64; ep_increment.cu) ------------------

@@ -614,6 +614,54 @@ def test_fused_fp32_matches_staged_fp32(P):
                 assert np.abs(out[k][f] - out[0][f]).max() / scale <= 2e-5, (k, f)
 
 
+def test_fused_check_iteration_matches_the_staged_check_fp32_3d(P):
+    """The FP32 register sweep's check iteration (the stopping measures
+    reduced inside the z-march, the check snapshots and centre scales
+    written by it) against the staged check iteration of the staged FP32
+    sweep: after 400 iterations of a plastic increment the measures of the
+    last check agree to the FP32 rounding of the two iterates, a solve to
+    tolerance takes the same number of check intervals, and a NaN in the
+    history ends the solve as diverged."""
+    s = E.config(3, n=(36, 30, 28), tol=1e-6, inclusion_radius=0.15)
+    infos, iters = [], []
+    for variant in (P.KERNEL_STAGED, P.KERNEL_FUSED_REG):
+        g = gpu_grid(P, s, P.FP32_MIXED, n_chk=100)
+        g.set_kernel(variant, 8)
+        for _ in range(4):
+            g.apply_increment(1.0, s.dt, P.LOAD_XZ)
+            g.solve_increment()
+        g.snapshot()
+        g.set_solver(tol=0.0, max_iter=400, n_chk=100)
+        g.apply_increment(1.0, s.dt, P.LOAD_XZ)
+        infos.append(g.solve_increment(raise_on_fail=False))
+        g.restore()
+        g.set_solver(tol=s.tol, max_iter=400000, n_chk=100)
+        g.apply_increment(1.0, s.dt, P.LOAD_XZ)
+        done = g.solve_increment()
+        assert done["n_plastic"] > 0          # a plastic increment
+        iters.append(done["iters"])
+        g.close()
+    a, b = infos
+    assert a["status"] == b["status"] == 5 and a["iters"] == b["iters"] == 400, (a, b)
+    assert abs(a["max_sigma"] - b["max_sigma"]) <= 1e-4 * a["max_sigma"]
+    for k in ("eps_mom", "eps_tau", "eps_p", "eps_rel", "max_r"):
+        assert abs(a[k] - b[k]) <= 5e-2 * max(abs(a[k]), 1e-30), (k, a[k], b[k])
+    assert abs(iters[0] - iters[1]) <= 100, iters
+    # a NaN in the old stress reaches the fused check at the first iteration
+    g = gpu_grid(P, s, P.FP32_MIXED, n_chk=100)
+    g.set_kernel(P.KERNEL_FUSED_REG, 8)
+    for _ in range(4):
+        g.apply_increment(1.0, s.dt, P.LOAD_XZ)
+        g.solve_increment()
+    bad = g.get("txx").copy()
+    bad[14, 15, 18] = np.nan
+    g.set("txx", bad)
+    g.apply_increment(1.0, s.dt, P.LOAD_XZ)
+    info = g.solve_increment(raise_on_fail=False)
+    assert info["status"] == 6 and info["iters"] == 0, info   # EP_ERR_DIVERGED at the first check
+    g.close()
+
+
 @pytest.mark.parametrize("tile,n", [(0, (70, 37)), (1, (70, 37)), (2, (70, 37)), (3, (70, 37)), (3, (30, 150)),
                                     (4, (70, 37))])
 def test_fused2d_fp64_parity(P, tile, n):
