@@ -76,6 +76,8 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--oracle-plan", action="store_true", help="time the CPU oracle per iteration and increment")
     ap.add_argument("--symmetry-study", action="store_true", help="the paper's large vs small increment study")
+    ap.add_argument("--warm-study", type=int, default=0, choices=[0, 2, 3],
+                    help="the learned warm start on held-out setups: trained vs zero network vs plain start (2D or 3D)")
     ap.add_argument("--sym-strain", type=float, default=1.4e-3, help="total strain of the symmetry study")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-size", type=int, default=48, help="edge of the oracle's sample box (CPU legs)")
@@ -268,6 +270,101 @@ def oracle_plan(args):
     return 0
 
 
+def warm_study(args):
+    """What the learned warm start gains on setups it was not trained on.
+    2D: 48^2 boxes with a weak inclusion at varying positions and varying
+    friction angle and cohesion, a base-16 network trained on six setups x
+    ten increments (800 Adam steps), three held-out setups.  3D: 63^3 boxes of
+    the benchmark's setup (other seeds and cohesions), a base-32 network on
+    four setups x ten increments (1500 steps), three held-out setups, checks
+    every 1000 iterations.  Each held-out increment from the third on is
+    solved from the same device checkpoint with the trained network, with the
+    zero network (its output is the plain start) and with the plain start;
+    the plain solve is kept.  Prints one JSON object."""
+    import numpy as np
+    import torch
+    import ep_inputs as E
+    import paper_2305_01701_gb300 as P
+    from paper_2305_01701_gb300 import warmstart as W
+    nd = args.warm_study
+    t0 = time.perf_counter()
+    if nd == 2:
+        n, incs, steps, base, plane, nchk, kernel = (48, 48), 12, 800, 16, P.LOAD_XY, 100, None
+
+        def setup(q, sd):
+            return E.Setup("ws%d" % sd, 2, n, phi_deg=25.0 + 2 * (q % 4), c0=1.3e-3 + 1e-4 * (q % 4),
+                           inclusion_radius=0.08, inclusion_centre=(0.03 * ((q % 5) - 2), -0.02 * ((q % 3) - 1), 0.0),
+                           seed=sd, tol=1e-6)
+        train = [setup(q, 101 + q) for q in range(6)]
+        held = [setup(q, 201 + q) for q in range(3)]
+    else:
+        n, incs, steps, base, plane, nchk, kernel = (63, 63, 63), 12, 1500, 32, P.LOAD_XZ, 1000, P.KERNEL_FUSED_REG
+        ref = E.config(5, n=n, tol=1e-6)
+
+        def setup(k):
+            return E.config(5, n=n, tol=1e-6, seed=ref.seed + k, c0=ref.c0 * (1.0 + 0.04 * (k % 4)))
+        train = [setup(101 + q) for q in range(4)]
+        held = [setup(201 + q) for q in range(3)]
+    max_iter = 400000
+
+    def grid(s):
+        g = P.Grid(nd, s.n, precision=P.FP32_MIXED)
+        if kernel is not None:
+            g.set_kernel(kernel, 0)
+        g.set_material(s.K, s.G, s.mu_s, s.phi_deg, s.psi_deg, s.cohesion())
+        g.set_solver(tol=s.tol, max_iter=max_iter, n_chk=nchk)
+        return g
+
+    groups = []
+    for s in train:
+        g = grid(s)
+        d = W.Samples(nd, g.warm_dims(1), capacity=incs)
+        W.collect(g, s.a, s.dt, incs, d, load_plane=plane)
+        g.close()
+        groups.append(d)
+    net = W.new_net(nd, base=base, levels=3, seed=7)
+    zero = W.new_net(nd, base=base, levels=3, seed=7)
+    scale = W.calibrate(net, groups)
+    zero.set_output_scale(scale)
+    before = W.evaluate(net, groups)
+    W.train(net, groups, steps=steps, lr=1e-3, batch=2 if nd == 3 else 8, calibrate_scale=False)
+    after = W.evaluate(net, groups)
+    t_train = time.perf_counter() - t0
+    total = {"trained": 0, "zero": 0, "plain": 0}
+    rows = []
+    for s in held:
+        g = grid(s)
+        for inc in range(1, incs + 1):
+            if inc < 3:
+                g.apply_increment(s.a, s.dt, plane)
+                g.solve_increment()
+                continue
+            g.snapshot()
+            out = {}
+            for name, nn in (("trained", net), ("zero", zero), ("plain", None)):
+                if nn is not None:
+                    g.attach_warm_start(nn, 1)
+                g.apply_increment(s.a, s.dt, plane, use_warm_start=nn is not None)
+                info = g.solve_increment(raise_on_fail=False)
+                out[name] = info["iters"] if info["status"] == 0 else max_iter
+                total[name] += out[name]
+                if name != "plain":
+                    g.restore()
+                elif info["status"] != 0:
+                    raise RuntimeError("plain solve failed at increment %d of %s" % (inc, s.name))
+            rows.append({"setup": s.name, "increment": inc, **out})
+        g.close()
+    torch.cuda.synchronize()
+    res = {"study": "warm start %dD" % nd, "grid": "x".join(map(str, n)), "train_setups": len(train),
+           "held_out_setups": len(held), "increments": incs, "adam_steps": steps, "base": base,
+           "check_every": nchk, "output_scale": scale, "loss_before": before, "loss_after": after,
+           "loss_unit": "mean square of the training targets", "train_seconds": t_train,
+           "total_iterations": total, "rows": rows, "seconds": time.perf_counter() - t0}
+    print(json.dumps(res))
+    del np
+    return 0
+
+
 def symmetry_study(args):
     """The paper's symmetry study (Sec. 4.3) on the GPU: the 383 x 191 box
     with a central pressure anomaly (no Jaumann term, elastic limit), loaded
@@ -407,9 +504,12 @@ def aggregate(torch, dist, seconds, units, device):
 # dominant kernel from one ncu capture of the benchmark command, by kernel and
 # box size; the entry must be dropped when the kernel changes.
 # DRAM bytes per launch of the dominant kernel from an ncu capture of its
-# current build (filled from profiles/ once captured; null until then)
-NCU_TRAFFIC = {}
-NCU_SOURCE = {}
+# current build (profiles/k_fused3d_reg_127cube.md)
+NCU_TRAFFIC = {("k_fused3d_reg", 127): 271.3e6,
+               ("k_fused3d_reg", 511): 271.3e6 * 133432831 / 2048383}
+NCU_SOURCE = {("k_fused3d_reg", 127): "ncu --set full capture of one launch at 127^3 (profiles/)",
+              ("k_fused3d_reg", 511): "ncu --set full capture of one launch at 127^3 (profiles/), the per-cell "
+                                      "traffic scaled to 511^3 by the cell count"}
 # FP64 flops per cell of one staged FP64 sweep (dadd + dmul + 2 dfma thread
 # instructions of its five kernels, counted by ncu at 127^3; profiles/)
 FP64_FLOPS_PER_CELL = 322.5
@@ -820,6 +920,8 @@ def main():
         return oracle_plan(args)
     if args.symmetry_study:
         return symmetry_study(args)
+    if args.warm_study:
+        return warm_study(args)
     if args.impl == "reference":
         return reference_arm(args)
     if args.batch > 0:

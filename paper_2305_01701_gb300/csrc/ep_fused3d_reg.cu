@@ -82,6 +82,9 @@ struct Args {
 
 template <typename T>
 __device__ __forceinline__ T maxt(T a, T b) { return (a > b || a != a) ? a : b; }
+// |x| in the type of x (no round trip through double for FP32)
+__device__ __forceinline__ float absv(float x) { return fabsf(x); }
+__device__ __forceinline__ double absv(double x) { return fabs(x); }
 
 // block-wide max of a non-negative value as its IEEE bits (integer order; a
 // NaN sorts above infinity), one atomic per block
@@ -342,10 +345,10 @@ __device__ __forceinline__ void reg_body(const Args<T> &A, const Geo &g, const S
           A.snn[0][ec] = n0; A.snn[1][ec] = n1; A.snn[2][ec] = n2; A.snp[ec] = pr;
           if constexpr (CHK) {   // a centre of the box (lc < nz, gi < nx, gj < ny hold here)
             if (!frozen) A.s[ec] = s_1;
-            c_sig = maxt(c_sig, maxt((T)fabs(n0 - pr), maxt((T)fabs(n1 - pr), (T)fabs(n2 - pr))));
-            c_dtau = maxt(c_dtau, maxt((T)fabs(n0 - A.cn[0][ec]),
-                                       maxt((T)fabs(n1 - A.cn[1][ec]), (T)fabs(n2 - A.cn[2][ec]))));
-            c_dp = maxt(c_dp, (T)fabs(pr - A.cp[ec]));
+            c_sig = maxt(c_sig, maxt(absv(n0 - pr), maxt(absv(n1 - pr), absv(n2 - pr))));
+            c_dtau = maxt(c_dtau, maxt(absv(n0 - A.cn[0][ec]),
+                                       maxt(absv(n1 - A.cn[1][ec]), absv(n2 - A.cn[2][ec]))));
+            c_dp = maxt(c_dp, absv(pr - A.cp[ec]));
             A.cn[0][ec] = n0; A.cn[1][ec] = n1; A.cn[2][ec] = n2; A.cp[ec] = pr;
             if (isnan(s_1) || isnan(pr)) c_sig = (T)NAN;
           }
@@ -375,9 +378,9 @@ __device__ __forceinline__ void reg_body(const Args<T> &A, const Geo &g, const S
         A.sns[0][e] = nxy_1; A.sns[1][e] = nxz_1; A.sns[2][e] = nyz_1;
         if constexpr (CHK) {
           if (gi <= g.nx && gj <= g.ny && lc <= nz) {   // the staged check's edge points
-            c_sig = maxt(c_sig, maxt((T)fabs(nxy_1), maxt((T)fabs(nxz_1), (T)fabs(nyz_1))));
-            c_dtau = maxt(c_dtau, maxt((T)fabs(nxy_1 - A.cs[0][e]),
-                                       maxt((T)fabs(nxz_1 - A.cs[1][e]), (T)fabs(nyz_1 - A.cs[2][e]))));
+            c_sig = maxt(c_sig, maxt(absv(nxy_1), maxt(absv(nxz_1), absv(nyz_1))));
+            c_dtau = maxt(c_dtau, maxt(absv(nxy_1 - A.cs[0][e]),
+                                       maxt(absv(nxz_1 - A.cs[1][e]), absv(nyz_1 - A.cs[2][e]))));
             A.cs[0][e] = nxy_1; A.cs[1][e] = nxz_1; A.cs[2][e] = nyz_1;
           }
         }
@@ -397,13 +400,13 @@ __device__ __forceinline__ void reg_body(const Args<T> &A, const Geo &g, const S
         if (gx1 && gyl && lu < nz) {
           const T R = (sxx_2 - sxx_2_xm) * rdx + (nxy_2_yp - nxy_2) * rdy + (nxz_1 - nxz_2) * rdz;
           un = u0_2 + vs * R;
-          if constexpr (CHK) c_r = maxt(c_r, (T)fabs(R));
+          if constexpr (CHK) c_r = maxt(c_r, absv(R));
         }
         A.uo[0][e] = un;
         if constexpr (CHK) {
           if (gi <= g.nx && gj < g.ny && lu < nz) {   // x-faces
-            c_du = maxt(c_du, (T)fabs(un - A.uchk[0][e]));
-            c_vm = maxt(c_vm, fabs(A.v0[0][e] + (double)u0_2));
+            c_du = maxt(c_du, absv(un - A.uchk[0][e]));
+            c_vm = fmax(c_vm, fabs(A.v0[0][e] + (double)u0_2));   // a NaN in u also reaches c_du
             A.uchk[0][e] = un;
           }
         }
@@ -411,13 +414,13 @@ __device__ __forceinline__ void reg_body(const Args<T> &A, const Geo &g, const S
         if (gy1 && gxl && lu < nz) {
           const T R = (syy_2 - syy_2_ym) * rdy + (nxy_2_xp - nxy_2) * rdx + (nyz_1 - nyz_2) * rdz;
           un = u1_2 + vs * R;
-          if constexpr (CHK) c_r = maxt(c_r, (T)fabs(R));
+          if constexpr (CHK) c_r = maxt(c_r, absv(R));
         }
         A.uo[1][e] = un;
         if constexpr (CHK) {
           if (gi < g.nx && gj <= g.ny && lu < nz) {   // y-faces
-            c_du = maxt(c_du, (T)fabs(un - A.uchk[1][e]));
-            c_vm = maxt(c_vm, fabs(A.v0[1][e] + (double)u1_2));
+            c_du = maxt(c_du, absv(un - A.uchk[1][e]));
+            c_vm = fmax(c_vm, fabs(A.v0[1][e] + (double)u1_2));
             A.uchk[1][e] = un;
           }
         }
@@ -425,13 +428,13 @@ __device__ __forceinline__ void reg_body(const Args<T> &A, const Geo &g, const S
         if (lu >= 1 && lu <= nz - 1 && gxl && gyl) {
           const T R = (szz_2 - szz_3) * rdz + (nxz_2_xp - nxz_2) * rdx + (nyz_2_yp - nyz_2) * rdy;
           un = u2_2 + vs * R;
-          if constexpr (CHK) c_r = maxt(c_r, (T)fabs(R));
+          if constexpr (CHK) c_r = maxt(c_r, absv(R));
         }
         A.uo[2][e] = un;
         if constexpr (CHK) {
           if (gi < g.nx && gj < g.ny && lu <= nz) {   // z-faces
-            c_du = maxt(c_du, (T)fabs(un - A.uchk[2][e]));
-            c_vm = maxt(c_vm, fabs(A.v0[2][e] + (double)u2_2));
+            c_du = maxt(c_du, absv(un - A.uchk[2][e]));
+            c_vm = fmax(c_vm, fabs(A.v0[2][e] + (double)u2_2));
             A.uchk[2][e] = un;
           }
         }
