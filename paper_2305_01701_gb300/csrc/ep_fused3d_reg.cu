@@ -35,7 +35,10 @@
 // and the same snapshot updates as the staged check iteration: max|sigma|,
 // max|tau - tau_chk|, max|p - p_chk| at centres and edges, max|R|,
 // max|u - u_chk| and max|v0 + u| at faces, and they store the centre scales
-// (held when plasticity freezes).  One atomic per block and measure.
+// (held when plasticity freezes).  One atomic per block and measure.  The
+// snapshot values a thread checks in a plane are copied to shared memory with
+// cp.async at the plane's start and read after the second barrier, so that
+// their memory latency hides behind the plane's first steps.
 #include <math.h>
 
 #include <type_traits>
@@ -80,6 +83,24 @@ struct Args {
   const double *v0[3];               // start velocity (check iterations)
 };
 
+// a check iteration's snapshot values, one slot per thread, after SmemR
+template <typename T, int H>
+struct ChkSlots {
+  T cn[3][WX * H], cs[3][WX * H], cp[WX * H], uchk[3][WX * H];
+  double v0[3][WX * H];
+};
+
+__device__ __forceinline__ void cp_async_el(float *smem, const float *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_el(double *smem, const double *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::); }
+
 template <typename T>
 __device__ __forceinline__ T maxt(T a, T b) { return (a > b || a != a) ? a : b; }
 // |x| in the type of x (no round trip through double for FP32)
@@ -118,6 +139,7 @@ template <typename T, int H, bool INT, typename Off, bool CHK>
 __device__ __forceinline__ void reg_body(const Args<T> &A, const Geo &g, const Scal *sc, DevInfo *di, bool frozen,
                                          int kz, unsigned char *smem_raw) {
   SmemR<T, H> &S = *reinterpret_cast<SmemR<T, H> *>(smem_raw);
+  ChkSlots<T, H> &C = *reinterpret_cast<ChkSlots<T, H> *>(smem_raw + sizeof(SmemR<T, H>));   // CHK only
   constexpr int W = WX;
   const int a = threadIdx.x & 31, b = threadIdx.x >> 5;
   const int i0 = blockIdx.x * OX, j0 = blockIdx.y * (H - 4);
@@ -211,6 +233,19 @@ __device__ __forceinline__ void reg_body(const Args<T> &A, const Geo &g, const S
     const T soxy = n_soxy, tbxy = n_tbxy, sop = n_sop, pb = n_pb, yc = n_yc;
     const bool more = t + 1 < ke + 2;
     if (more) prefetch(t + 1);
+    if constexpr (CHK) {   // the snapshot values checked at this plane: levels t-1 (centres, edges), t-2 (faces)
+      const int tid = threadIdx.x;
+      const Off e1 = (Off)min(max(t - 1, 0), pz - 1) * plane + col, e2 = (Off)min(max(t - 2, 0), pz - 1) * plane + col;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        cp_async_el(&C.cn[d][tid], A.cn[d] + e1);
+        cp_async_el(&C.cs[d][tid], A.cs[d] + e1);
+        cp_async_el(&C.uchk[d][tid], A.uchk[d] + e2);
+        cp_async_el(&C.v0[d][tid], A.v0[d] + e2);
+      }
+      cp_async_el(&C.cp[tid], A.cp + e1);
+      cp_async_commit();
+    }
 
     // ---- 1. shear strain rates and spins at plane t (xy) / face t (xz, yz) ----
     T exy = 0, oxy = 0, exz = 0, oxz = 0, eyz = 0, oyz = 0;
@@ -311,6 +346,7 @@ __device__ __forceinline__ void reg_body(const Args<T> &A, const Geo &g, const S
 
     // ---- 3. pressure and return at the centres of plane t-1 ----
     T s_1 = 0, sxx_1 = 0, syy_1 = 0, szz_1 = 0;
+    if constexpr (CHK) cp_async_wait_all();   // this thread's own slots
     if (b >= 1 && b < H - 1) {
       const T tsxy_xp = xp(tsxy), tsxy_yp = S.tsxy.r[rb + 1][a];
       const T tsxy_yp_xp = xp(tsxy_yp);
@@ -346,9 +382,10 @@ __device__ __forceinline__ void reg_body(const Args<T> &A, const Geo &g, const S
           if constexpr (CHK) {   // a centre of the box (lc < nz, gi < nx, gj < ny hold here)
             if (!frozen) A.s[ec] = s_1;
             c_sig = maxt(c_sig, maxt(absv(n0 - pr), maxt(absv(n1 - pr), absv(n2 - pr))));
-            c_dtau = maxt(c_dtau, maxt(absv(n0 - A.cn[0][ec]),
-                                       maxt(absv(n1 - A.cn[1][ec]), absv(n2 - A.cn[2][ec]))));
-            c_dp = maxt(c_dp, absv(pr - A.cp[ec]));
+            const int tid = threadIdx.x;
+            c_dtau = maxt(c_dtau, maxt(absv(n0 - C.cn[0][tid]),
+                                       maxt(absv(n1 - C.cn[1][tid]), absv(n2 - C.cn[2][tid]))));
+            c_dp = maxt(c_dp, absv(pr - C.cp[tid]));
             A.cn[0][ec] = n0; A.cn[1][ec] = n1; A.cn[2][ec] = n2; A.cp[ec] = pr;
             if (isnan(s_1) || isnan(pr)) c_sig = (T)NAN;
           }
@@ -379,8 +416,9 @@ __device__ __forceinline__ void reg_body(const Args<T> &A, const Geo &g, const S
         if constexpr (CHK) {
           if (gi <= g.nx && gj <= g.ny && lc <= nz) {   // the staged check's edge points
             c_sig = maxt(c_sig, maxt(absv(nxy_1), maxt(absv(nxz_1), absv(nyz_1))));
-            c_dtau = maxt(c_dtau, maxt(absv(nxy_1 - A.cs[0][e]),
-                                       maxt(absv(nxz_1 - A.cs[1][e]), absv(nyz_1 - A.cs[2][e]))));
+            const int tid = threadIdx.x;
+            c_dtau = maxt(c_dtau, maxt(absv(nxy_1 - C.cs[0][tid]),
+                                       maxt(absv(nxz_1 - C.cs[1][tid]), absv(nyz_1 - C.cs[2][tid]))));
             A.cs[0][e] = nxy_1; A.cs[1][e] = nxz_1; A.cs[2][e] = nyz_1;
           }
         }
@@ -405,8 +443,8 @@ __device__ __forceinline__ void reg_body(const Args<T> &A, const Geo &g, const S
         A.uo[0][e] = un;
         if constexpr (CHK) {
           if (gi <= g.nx && gj < g.ny && lu < nz) {   // x-faces
-            c_du = maxt(c_du, absv(un - A.uchk[0][e]));
-            c_vm = fmax(c_vm, fabs(A.v0[0][e] + (double)u0_2));   // a NaN in u also reaches c_du
+            c_du = maxt(c_du, absv(un - C.uchk[0][threadIdx.x]));
+            c_vm = fmax(c_vm, fabs(C.v0[0][threadIdx.x] + (double)u0_2));   // a NaN in u also reaches c_du
             A.uchk[0][e] = un;
           }
         }
@@ -419,8 +457,8 @@ __device__ __forceinline__ void reg_body(const Args<T> &A, const Geo &g, const S
         A.uo[1][e] = un;
         if constexpr (CHK) {
           if (gi < g.nx && gj <= g.ny && lu < nz) {   // y-faces
-            c_du = maxt(c_du, absv(un - A.uchk[1][e]));
-            c_vm = fmax(c_vm, fabs(A.v0[1][e] + (double)u1_2));
+            c_du = maxt(c_du, absv(un - C.uchk[1][threadIdx.x]));
+            c_vm = fmax(c_vm, fabs(C.v0[1][threadIdx.x] + (double)u1_2));
             A.uchk[1][e] = un;
           }
         }
@@ -433,8 +471,8 @@ __device__ __forceinline__ void reg_body(const Args<T> &A, const Geo &g, const S
         A.uo[2][e] = un;
         if constexpr (CHK) {
           if (gi < g.nx && gj < g.ny && lu <= nz) {   // z-faces
-            c_du = maxt(c_du, absv(un - A.uchk[2][e]));
-            c_vm = fmax(c_vm, fabs(A.v0[2][e] + (double)u2_2));
+            c_du = maxt(c_du, absv(un - C.uchk[2][threadIdx.x]));
+            c_vm = fmax(c_vm, fabs(C.v0[2][threadIdx.x] + (double)u2_2));
             A.uchk[2][e] = un;
           }
         }
@@ -501,12 +539,12 @@ void launch_fused3d_reg(const Geo &g, const Stage<T> &S, const Scal *sc, DevInfo
   A.s = S.s; A.cp = S.cp;
   kz = fused3d_kz(g, OX, H - 4, kz);
   dim3 grid((g.px + OX - 1) / OX, (g.py + H - 5) / (H - 4), (g.pz + kz - 1) / kz);
-  const size_t sm = sizeof(SmemR<T, H>);
+  const size_t sm = sizeof(SmemR<T, H>), smc = sm + sizeof(ChkSlots<T, H>);
   if constexpr (sizeof(T) == 4) {
     const bool o32 = (long long)g.pz * g.plane < (1LL << 31);
     if (check) {
-      if (o32) k_fused3d_reg<T, H, int, true><<<grid, WX * H, sm, st>>>(A, g, sc, di, kz);
-      else k_fused3d_reg<T, H, long long, true><<<grid, WX * H, sm, st>>>(A, g, sc, di, kz);
+      if (o32) k_fused3d_reg<T, H, int, true><<<grid, WX * H, smc, st>>>(A, g, sc, di, kz);
+      else k_fused3d_reg<T, H, long long, true><<<grid, WX * H, smc, st>>>(A, g, sc, di, kz);
     } else {
       if (o32) k_fused3d_reg<T, H, int, false><<<grid, WX * H, sm, st>>>(A, g, sc, di, kz);
       else k_fused3d_reg<T, H, long long, false><<<grid, WX * H, sm, st>>>(A, g, sc, di, kz);
@@ -517,17 +555,17 @@ void launch_fused3d_reg(const Geo &g, const Stage<T> &S, const Scal *sc, DevInfo
 }
 
 cudaError_t fused3d_reg_configure() {
-  const int sf = (int)sizeof(SmemR<float, 16>);
+  const int sf = (int)sizeof(SmemR<float, 16>), sfc = sf + (int)sizeof(ChkSlots<float, 16>);
   cudaError_t e = cudaFuncSetAttribute(k_fused3d_reg<float, 16, int, false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, sf);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_fused3d_reg<float, 16, long long, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              sf);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_fused3d_reg<float, 16, int, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sf);
+    e = cudaFuncSetAttribute(k_fused3d_reg<float, 16, int, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sfc);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_fused3d_reg<float, 16, long long, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             sf);
+                             sfc);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_fused3d_reg<double, 8, long long, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)sizeof(SmemR<double, 8>));
