@@ -315,13 +315,15 @@ def warm_study(args):
         g.set_solver(tol=s.tol, max_iter=max_iter, n_chk=nchk)
         return g
 
-    groups = []
+    # one pool of samples: a minibatch of consecutive samples spans setups
+    data = None
     for s in train:
         g = grid(s)
-        d = W.Samples(nd, g.warm_dims(1), capacity=incs)
-        W.collect(g, s.a, s.dt, incs, d, load_plane=plane)
+        if data is None:
+            data = W.Samples(nd, g.warm_dims(1), capacity=len(train) * incs)
+        W.collect(g, s.a, s.dt, incs, data, load_plane=plane)
         g.close()
-        groups.append(d)
+    groups = [data]
     net = W.new_net(nd, base=base, levels=3, seed=7)
     zero = W.new_net(nd, base=base, levels=3, seed=7)
     scale = W.calibrate(net, groups)
