@@ -215,7 +215,11 @@ ep_status ep_set_fields(ep_handle h, int field, const double *host_in, size_t co
  * EP_KERNEL_FUSED_TMA is the 3D fused sweep with every plane streamed by
  * the tensor-memory accelerator (a timed-out copy ends the solve with
  * EP_ERR_TIMEOUT); EP_KERNEL_FUSED_REG is the 3D fused sweep that keeps the
- * z-march in registers (lanes own x columns, warps own y rows).  A body force always uses the staged sweep.
+ * z-march in registers (lanes own x columns, warps own y rows).  The check
+ * iteration of each chunk runs fused too with the FP32 register sweep (it
+ * reduces the stopping measures itself); the other 3D flavours and FP64
+ * grids take the staged sweep for it.  A body force always uses the staged
+ * sweep.
  * shape (< 0 keeps the current): in 3D the z-planes per block of the fused
  * kernels (0, the default: chosen from the grid size so that the launch
  * fills every SM); in 2D the tile of the fused kernel (0: 32x8, 1: 32x16,
