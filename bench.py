@@ -873,7 +873,8 @@ def batch_arm(args):
         nmin = min(x.n[0] for x in setups)
         small = max((q for q in range(len(setups)) if setups[q].n[0] == nmin), key=lambda q: iters[q])
         small = setups[small]
-        o = O.from_setup(small)
+        lib_path, thr = oracle_lib(args.oracle_threads)
+        o = O.from_setup(small, lib_path=lib_path)
         o.set_solver(tol=small.tol, max_iter=2000000, n_chk=100)
         if args.batch_freeze:
             o.set_freeze(16 * small.n[0], 1e-4)
@@ -886,9 +887,10 @@ def batch_arm(args):
         ot = _t.perf_counter() - t0
         ocells = small.n[0] * small.n[1]
         cpu = {"value": alg_bytes_per_cell(2, "fp64") * ocells * max(oi["iters"], 1) / ot / 1e9, "unit": "GB/s",
-               "cores": 1, "kind": "oracle",
-               "sample": "increment %d of one %dx%d instance (%s), single-threaded FP64 oracle, %d iterations "
-                         "in %.2f s" % (args.batch_increment, small.n[0], small.n[1], small.name, oi["iters"], ot)}
+               "cores": thr, "kind": "oracle",
+               "sample": "increment %d of one %dx%d instance (%s), FP64 oracle on %d thread(s), %d iterations "
+                         "in %.2f s" % (args.batch_increment, small.n[0], small.n[1], small.name, thr, oi["iters"],
+                                        ot)}
     line = {
         "metric": "aggregate sweep GB/s and wall time per batched increment to tol 1e-6",
         "value": gbs, "unit": "GB/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
