@@ -521,9 +521,9 @@ NCU_SOURCE = {("k_fused3d_reg", 127): "ncu --set full capture of one launch at 1
 # FP64 flops per cell of one staged FP64 sweep (dadd + dmul + 2 dfma thread
 # instructions of its five kernels, counted by ncu at 127^3; profiles/)
 FP64_FLOPS_PER_CELL = 322.5
-# the survey's algorithmic bytes per cell of a 3D FP32 sweep whose stress is
+# algorithmic bytes per cell of a 3D FP32 sweep recast so that its stress is
 # no pseudo-time state (reported beside the fraction by the scheme's bytes)
-SURVEY_BYTES_3D_FP32 = 80.0
+RECAST_BYTES_3D_FP32 = 80.0
 
 
 def kernel_names(ktimes, kernel):
@@ -755,7 +755,7 @@ def our_arm(args):
             "traffic_source": NCU_SOURCE.get((kernels[dom], s.n[0])),
             "kernel_ms": {k: float(ktimes[q]) for q, k in enumerate(kernels)},
             "dominant": kernels[dom], "iteration_ms": float(it_ms), "alg_bytes_per_cell": bpc,
-            "frac_survey_bytes": SURVEY_BYTES_3D_FP32 * cells / (it_ms * 1e-3) / 1e9 / hbm}
+            "frac_recast_bytes": RECAST_BYTES_3D_FP32 * cells / (it_ms * 1e-3) / 1e9 / hbm}
     warm_desc = "warm start (3D U-Net on coarse cells of %d^3)" % args.coarsen if net is not None else "plain start"
     line = {
         "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": world, "steps": args.steps,

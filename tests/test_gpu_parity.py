@@ -418,8 +418,7 @@ def test_not_converged_keeps_state_and_reports(P):
 
 
 def test_nan_in_the_history_is_reported_as_diverged_and_the_grid_recovers(P):
-    """Failure injection on the host (SURVEY's failure-detection plan, no GPU
-    fault): a NaN written into the old stress through ep_set_fields reaches
+    """Failure injection on the host (no GPU fault): a NaN written into the old stress through ep_set_fields reaches
     the residual norms, the solve returns EP_ERR_DIVERGED without
     committing, and the handle stays usable: with the finite history restored
     from a device checkpoint, the increment solves as on a grid that never
